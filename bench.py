@@ -1,0 +1,360 @@
+"""Benchmark of the partitioned synchronous Jacobi sweep on one GB300 (or N replicas).
+
+Workload (one "step"): the 160^3 7-point Laplace system (n = 4,096,000,
+nnz = 28,518,400, FP64 CSR, b = A x*, x* ~ U[-1,1] seed 0) swept 2000 times
+under each of the three splittings -- 64 row bands, 64 nnz-balanced bands,
+and 4x4x4 substructuring with the interface last -- i.e. 6000 fused
+sweep + residual-norm passes per step.  Inputs are resident in HBM; every
+sweep streams 440.5 MB (> L2), so no L2 flush is needed between steps.
+
+value  = algorithmic bytes of all sweeps / device time (GB/s, CUDA events on
+         the library's stream), summed over ranks, max time over ranks.
+e2e    = the same metric through the C ABI with pinned host buffers: per step
+         and splitting, b and x0 copied host->device, 2000 sweeps, x copied
+         device->host.
+Extra keys: time to relative residual 1e-8 (FP64 vs mixed FP32/FP64), the
+roofline of the dominant kernel, the CPU oracle baseline and SM clocks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = 160
+SWEEPS_PER_SPLIT = 2000
+SPLITS = [("bandrow", 64), ("bandrow_nnz", 64), ("substruct", 0)]
+SUBDOMAINS = (4, 4, 4)
+K_PER_GRAPH = 64
+TOL_TTR = 1e-8
+MIXED_INNER = 256
+
+
+def _algorithmic_bytes(n: int, nnz: int) -> float:
+    # FP64: 12 (nnz - n) [T + col] + 8n [diag] + 4(n+1) [IA] + 8n [c] + 8n [x in] + 8n [x out]
+    off = nnz - n
+    return 12.0 * off + 8.0 * n + 4.0 * (n + 1) + 8.0 * n + 8.0 * n + 8.0 * n
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [t.strip() for t in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_from_profile(kernel_src_hash: str):
+    """Per-sweep DRAM bytes of the sweep kernel from the committed ncu summary,
+    or None if the summary is missing or was taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "sweep_fp64_laplace7.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_sweep"])
+    except (KeyError, ValueError):
+        return None
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("jac_kernels.cu", "jac_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2112_02377_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _measured_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle --
+
+def cpu_oracle_rate(A, b, sweeps: int):
+    """The oracle's plain C sweep, single-threaded, on the same matrix."""
+    from oracle import oracle as O
+    Mo = O.prepare(A)
+    x = np.zeros(A.n)
+    y = None
+    t0 = time.perf_counter()
+    for _ in range(sweeps):
+        y, ss, mx = O.sweep(Mo, b, x)
+        x = y
+    dt = time.perf_counter() - t0
+    return dt
+
+
+# ------------------------------------------------------------------ main --
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from paper_2112_02377_gb300 import workloads as W
+    A = W.laplace7(GRID)
+    xs, b = W.solution_and_rhs(A, 0)
+    bps = _algorithmic_bytes(A.n, A.nnz)
+    per_step = 4     # sweeps of the oracle per step (a bounded sample of the 6000-sweep step)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(A, b, 1)
+    times = [cpu_oracle_rate(A, b, per_step) for _ in range(args.steps)]
+    t = sum(times)
+    value = bps * per_step * args.steps / t / 1e9
+    line = {
+        "impl": "reference", "metric": "jacobi_sweep_gbs_160cubed", "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * t / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "laplace7_160cubed_fp64_csr_2000_sweeps_x3_splittings", "grid": GRID,
+                   "sample": f"{per_step} oracle sweeps per step (of 6000)"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} FP64 sweeps of the 160^3 system per step, single-threaded C oracle"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-1e-8 solves")
+    ap.add_argument("--cpu-sweeps", type=int, default=200)
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    from paper_2112_02377_gb300 import jacobi as J
+    from paper_2112_02377_gb300 import workloads as W
+
+    A = W.laplace7(GRID)
+    xs, b = W.solution_and_rhs(A, 0)
+    bps = _algorithmic_bytes(A.n, A.nnz)
+    stream = torch.cuda.current_stream()
+    ctxs = []
+    setup_s = []
+    for split, P in SPLITS:
+        o = J.opts(variant=2, sweeps_per_graph=K_PER_GRAPH, stream=stream.cuda_stream, device=local)
+        if split == "substruct":
+            o.grid[:] = [GRID] * 3
+            o.subdomains[:] = list(SUBDOMAINS)
+        t0 = time.perf_counter()
+        ctxs.append(J.jac_setup(A, b, J.SPLITTINGS[split], P, o))
+        setup_s.append(time.perf_counter() - t0)
+    st0 = J.jac_stats(ctxs[0])
+    assert abs(st0["bytes_per_sweep_fp64"] - bps) < 1, (st0["bytes_per_sweep_fp64"], bps)
+
+    def step():
+        ms = 0.0
+        for c in ctxs:
+            J.jac_sweep(c, SWEEPS_PER_SPLIT)
+            ms += J.jac_stats(c)["last_ms"]
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp",
+                                        f"clocks_rank{rank}.csv"))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    kernel_ms = 0.0
+    for _ in range(args.steps):
+        kernel_ms += step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    sweeps = args.steps * SWEEPS_PER_SPLIT * len(SPLITS)
+    value = ws * bps * sweeps / (total_ms * 1e-3) / 1e9
+    launches_per_split = 1 + (SWEEPS_PER_SPLIT + K_PER_GRAPH - 1) // K_PER_GRAPH
+    gpu_launches = args.steps * len(SPLITS) * launches_per_split
+
+    # ---------------- roofline of the persistent sweep kernel: bytes of one
+    # full launch (K_PER_GRAPH sweeps) over its average duration, i.e. the
+    # algorithmic bytes of all timed sweeps over the CUDA-event time of the
+    # graph launches that ran them.
+    peak, peak_kind = _measured_peak()
+    achieved = bps * sweeps / (kernel_ms * 1e-3) / 1e9
+    khash = _kernel_hash()
+    traffic = _traffic_from_profile(khash)
+
+    # ---------------- end to end through the C ABI with pinned host buffers
+    xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+    bh = torch.from_numpy(b).pin_memory()
+    outs = [torch.empty(A.n, dtype=torch.float64).pin_memory() for _ in ctxs]
+    e2e_steps = max(1, min(args.steps, 3))
+
+    def e2e_step():
+        rels = []
+        for c, out in zip(ctxs, outs):
+            J.jac_set_b(c, bh)
+            J.jac_set_x(c, xh)
+            rels.append(J.jac_sweep(c, SWEEPS_PER_SPLIT))
+            J.jac_get_x(c, out)
+        return rels
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = ws * bps * e2e_steps * SWEEPS_PER_SPLIT * len(SPLITS) / e2e_s / 1e9
+    h2d = len(ctxs) * 2 * A.n * 8
+    d2h = len(ctxs) * (A.n * 8 + 8)
+
+    # ---------------- time to relative residual 1e-8: FP64 vs mixed
+    ttr = None
+    if not args.no_ttr:
+        ttr = {}
+        xref = None
+        for prec in ("fp64", "mixed"):
+            o = J.opts(variant=2, sweeps_per_graph=256, stream=stream.cuda_stream, device=local,
+                       precision=J.JAC_MIXED if prec == "mixed" else J.JAC_FP64, inner_sweeps=MIXED_INNER)
+            c = J.jac_setup(A, b, J.JAC_BANDROW, 64, o)
+            k, rel, stt = J.jac_solve(c, TOL_TTR, 200000)
+            st = J.jac_stats(c)
+            x = J.jac_get_x(c)
+            J.jac_free(c)
+            ttr[prec] = {"seconds": round(st["last_ms"] / 1e3, 4), "sweeps": k, "relres": rel,
+                         "status": int(stt)}
+            if prec == "fp64":
+                xref = x
+            else:
+                ttr[prec]["rel_err_vs_fp64"] = float(np.linalg.norm(x - xref) / np.linalg.norm(xref))
+                ttr[prec]["err_vs_xstar"] = float(np.linalg.norm(x - xs) / np.linalg.norm(xs))
+        ttr["fp64"]["err_vs_xstar"] = float(np.linalg.norm(xref - xs) / np.linalg.norm(xs))
+        ttr["speedup_mixed_over_fp64"] = round(ttr["fp64"]["seconds"] / ttr["mixed"]["seconds"], 3)
+        ttr["tol"] = TOL_TTR
+
+    # ---------------- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_sweeps > 0:
+        n_cpu = max(1, args.cpu_sweeps // 10)
+        dt = cpu_oracle_rate(A, b, n_cpu)
+        cpu = {"value": round(bps * n_cpu / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_cpu} FP64 sweeps of the 160^3 system (band-row order), single-threaded C oracle, "
+                         f"{dt:.1f} s"}
+
+    for c in ctxs:
+        J.jac_free(c)
+    if rank == 0:
+        line = {
+            "metric": "jacobi_sweep_gbs_160cubed", "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "laplace7_160cubed_fp64_csr_2000_sweeps_x3_splittings", "grid": GRID,
+                       "n": A.n, "nnz": A.nnz, "splittings": ["bandrow64", "bandrow_nnz64", "substruct4x4x4"],
+                       "sweeps_per_step": SWEEPS_PER_SPLIT * len(SPLITS), "sweeps_per_graph": K_PER_GRAPH,
+                       "l2": "inputs larger than L2 (440.5 MB streamed per sweep), no flush",
+                       "algorithmic_bytes_per_sweep": bps, "setup_seconds": [round(s, 3) for s in setup_s],
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                         "traffic": (traffic * K_PER_GRAPH if traffic is not None else None),
+                         "traffic_per_sweep": traffic, "kernel": "k_persistent<256,4,false>",
+                         "units_per_launch": K_PER_GRAPH, "bytes_per_unit": bps,
+                         "frac_of_8TBs": round(achieved / 8000.0, 4)},
+            "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": gpu_launches,
+            "time_to_relres_1e-8": ttr,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "kernel_source_sha256_16": khash,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,282 @@
+/*
+ * jacobi.h -- C ABI of the GB300 partitioned synchronous Jacobi solver.
+ *
+ * The library solves A x = b (paper Sec. 1, Eq. (1.1)) for a real square
+ * sparse matrix A given in CSR form (Sec. 4.1) by the synchronous Jacobi
+ * iteration x^{k+1} = D^{-1}(b - (L+U) x^k) (Sec. 3, Eqs. (3.4)-(3.5)),
+ * fused with the residual norm ||b - A x^k|| of every sweep (Algorithm 1).
+ * Rows are distributed by one of the paper's three splittings (Sec. 4):
+ * band-row, band-row balanced by non-zeros (the sparsity-pattern splitting
+ * with dependency lists), or substructuring with subdomain interiors first and
+ * the interface block last (Sec. 4.3, Eq. (4.4)).  On one GPU every partition
+ * is worked by a group of CTAs; the iterates do not depend on the splitting.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a jac_status; nothing throws across the ABI.
+ *     jac_last_error(ctx) returns a message for the last failure on ctx
+ *     (jac_last_error(NULL): the last failure of jac_setup* on this thread).
+ *   - Pointers tagged JAC_MEM_HOST are ordinary host memory; JAC_MEM_DEVICE
+ *     pointers are device memory on the context's device.  The library
+ *     never keeps a caller pointer after the call returns: inputs are
+ *     copied, outputs are written before return.
+ *   - All device work is issued on the stream given in jac_opts.stream
+ *     (NULL = the legacy default stream) and every call that returns results
+ *     synchronises that stream before returning.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef JACOBI_GB300_H
+#define JACOBI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jac_ctx jac_ctx;   /* opaque; owns all device memory and graphs */
+
+typedef enum {
+    JAC_OK = 0,
+    JAC_EINVAL = 1,      /* invalid argument (shape, index, option, size) */
+    JAC_ENOMEM = 2,      /* device or host allocation failed */
+    JAC_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+    JAC_ESINGULAR = 4,   /* a diagonal entry a_ii is missing or zero (D not invertible, Sec. 3) */
+    JAC_ENOTCONV = 5,    /* maxit reached before the tolerance; x holds the last iterate */
+    JAC_ETIMEOUT = 6,    /* a bounded device wait (grid barrier) gave up; iterate undefined */
+    JAC_ENUMERIC = 7     /* a residual became NaN or Inf (divergence, rho(T) >= 1) */
+} jac_status;
+
+typedef enum {
+    JAC_BANDROW = 0,      /* Sec. 4.2: band p = rows [floor(p n/P), floor((p+1) n/P)) */
+    JAC_BANDROW_NNZ = 1,  /* Sec. 4.2.2: contiguous bands balanced by non-zeros:
+                             boundary k = min{ r : P * IA(r) >= k * nnz } */
+    JAC_SUBSTRUCT = 2     /* Sec. 4.3: geometric boxes, one separator node plane per cut at
+                             floor(t g / p); interiors of subdomains 0..S-1, then the interface */
+} jac_splitting;
+
+typedef enum { JAC_MEM_HOST = 0, JAC_MEM_DEVICE = 1 } jac_memory;
+
+typedef enum {
+    JAC_FP64 = 0,         /* every sweep in FP64 */
+    JAC_MIXED = 1         /* FP32 sweeps inside FP64 residual/correction refinement */
+} jac_precision;
+
+typedef enum {
+    JAC_NORM_REL2 = 2,    /* test ||b - A x^k||_2 / ||b||_2 <= tol (||r||_2 if b == 0) */
+    JAC_NORM_INF = 0      /* test ||b - A x^k||_inf <= tol (absolute; Sec. 5.2 criterion
+                             ||D(x^{k+1} - x^k)||_inf, which equals it) */
+} jac_norm;
+
+/* Square sparse matrix in CSR form (Sec. 4.1: AA = val, JA = col, IA = rowptr).
+ * rowptr has n+1 entries, rowptr[0] == index_base, rowptr[n] == nnz + index_base;
+ * col/val have nnz entries; index_base is 0 or 1 (the paper prints 1-based
+ * arrays).  Entries of a row may come in any column order: each row's
+ * off-diagonal terms are summed in the stored order.  Exactly one entry per
+ * row may sit on the diagonal and it must be non-zero.  nnz < 2^31. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const double* val;
+    int32_t index_base;   /* 0 or 1 */
+    int32_t memory;       /* jac_memory of rowptr/col/val */
+} jac_csr;
+
+/* Options.  Fill with jac_opts_default() and change what you need; passing
+ * NULL anywhere an opts pointer is accepted means the defaults. */
+typedef struct {
+    int32_t precision;         /* jac_precision (default JAC_FP64) */
+    int32_t norm;              /* jac_norm (default JAC_NORM_REL2) */
+    int32_t sweeps_per_graph;  /* sweeps per CUDA-graph launch, 1..4096 (default 64) */
+    int32_t inner_sweeps;      /* JAC_MIXED: FP32 sweeps per FP64 refinement step, >= 1 (default 128) */
+    int32_t grid[3];           /* node grid (gx, gy, gz); required for JAC_SUBSTRUCT */
+    int32_t subdomains[3];     /* boxes per axis (px, py, pz); JAC_SUBSTRUCT only */
+    const int64_t* node_of_row;/* host array, n entries: grid node i + gx (j + gy k) of each row;
+                                  NULL = row r sits at node r */
+    int32_t nrhs;              /* right-hand sides sharing A (1..8, default 1) */
+    int32_t transpose;         /* 1 = solve with A^T instead of A (adjoint solves) */
+    int32_t variant;           /* 0 = auto; 1 = one launch per sweep (row kernel);
+                                  2 = persistent grid-synchronised pipelined kernel */
+    int32_t tile_rows;         /* rows per tile: 0 = auto, 256 or 512 */
+    int32_t history;           /* >0: record the relres of every evaluated iterate,
+                                  up to this many entries (jac_get_history) */
+    void* stream;              /* cudaStream_t for all work; NULL = legacy default stream */
+    uint64_t timeout_cycles;   /* bound of every device-side wait, in SM clock cycles
+                                  (0 = default, about 2 s) */
+    int32_t fault_skip_cta;    /* test hook: this CTA never arrives at the grid barrier,
+                                  so the others time out (-1 = off) */
+    int32_t device;            /* CUDA device ordinal; -1 = the current device */
+} jac_opts;
+
+/* Statistics of a context (jac_stats). */
+typedef struct {
+    int64_t n, nnz;               /* rows and stored entries of A (incl. diagonal) */
+    int64_t nparts;               /* partitions of the splitting (SUBSTRUCT: S interiors + 1) */
+    int64_t interface_rows;       /* SUBSTRUCT: rows of the interface block */
+    int64_t ntiles, ctas;         /* row tiles and CTAs of the sweep kernel */
+    int64_t halo_entries;         /* sum over partitions of received x entries (Sec. 4.2.2) */
+    int64_t max_row;              /* longest row (stored entries) */
+    int64_t k;                    /* index of the current iterate x^k */
+    int64_t sweeps_total;         /* sweeps evaluated since setup / jac_set_x */
+    int64_t outer_iterations;     /* JAC_MIXED refinement steps of the last solve */
+    double last_relres;           /* test value of the last evaluated iterate */
+    double last_res2, last_resinf;/* ||r||_2 and ||r||_inf of that iterate */
+    double last_ms;               /* device time of the last jac_sweep/jac_solve (CUDA events) */
+    double bytes_per_sweep_fp64;  /* algorithmic HBM bytes of one FP64 sweep */
+    double bytes_per_sweep_fp32;  /* algorithmic HBM bytes of one FP32 inner sweep */
+    int32_t variant, precision, splitting, nrhs;
+} jac_stats_t;
+
+/* Defaults for every option. */
+void jac_opts_default(jac_opts* o);
+
+/*
+ * jac_setup -- validate A, split and reorder it, upload it, build the graphs.
+ *
+ * Paper: problem statement Sec. 1 Eq. (1.1) (inputs n, A, b; Algorithm 1's
+ * D^{-1} "computed once before the iterations"); splittings Sec. 4.2-4.3.
+ *   A       square CSR matrix (see jac_csr), host or device memory.
+ *   b       right-hand sides, n*nrhs doubles, row-major (b[i*nrhs + c]),
+ *           in A->memory; NULL means b = 0.
+ *   s       splitting; nparts = number of bands for the band splittings
+ *           (1 <= nparts <= n); ignored for JAC_SUBSTRUCT, whose partitions
+ *           are the px*py*pz subdomain interiors plus the interface.
+ *   o       options (NULL = defaults).
+ *   out     receives the new context; *out = NULL on failure.
+ * Initial iterate x^0 = 0.
+ * Errors: JAC_EINVAL (n < 1, bad indices, duplicate diagonal, nparts out of
+ * range, SUBSTRUCT without grid/subdomains, a grid that does not decouple
+ * the subdomain interiors, nnz >= 2^31), JAC_ESINGULAR (zero or missing
+ * diagonal), JAC_ENOMEM, JAC_ECUDA.
+ */
+jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts,
+                     const jac_opts* o, jac_ctx** out);
+
+/*
+ * jac_setup_batched -- nsys independent systems, solved together.
+ *
+ * Paper: the same iteration (Sec. 3) applied to a block-diagonal system;
+ * every system keeps its own residual norm and convergence test.
+ *   A[s], b[s]   system s (n_s rows, b[s] is n_s*nrhs row-major), all in
+ *                A[0].memory; systems are band-split with one band each.
+ *   nsys         1 <= nsys <= 65536.
+ * jac_get_x returns the concatenation of the systems' solutions;
+ * jac_get_batch_results the per-system sweeps and residuals.
+ * Errors as jac_setup.
+ */
+jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const* b,
+                             const jac_opts* o, jac_ctx** out);
+
+/*
+ * jac_set_x -- set the current iterate x^0 (warm start / resume; Algorithm 1
+ * input u^(0)).  x: n*nrhs doubles row-major in the ORIGINAL row order, in
+ * `memory`; NULL = zero.  Resets k and sweeps_total to 0.
+ */
+jac_status jac_set_x(jac_ctx* ctx, const double* x, int32_t memory);
+
+/*
+ * jac_set_b -- replace the right-hand side (same layout as in jac_setup);
+ * keeps the current iterate.  NULL = zero.
+ */
+jac_status jac_set_b(jac_ctx* ctx, const double* b, int32_t memory);
+
+/*
+ * jac_sweep -- apply exactly k >= 0 synchronous sweeps, no convergence test.
+ *
+ * Paper: one pass of Algorithm 1's loop body per sweep (q = A x, r = b - q,
+ * ||r||, x += D^{-1} r) in the form of Eq. (3.4).  After the call the context
+ * holds x^{k0+k}.  relres_out (may be NULL) receives the test value
+ * (jac_opts.norm) of the last pre-update iterate x^{k0+k-1}
+ * (unchanged if k == 0).  For JAC_MIXED contexts a sweep is one FP64 sweep.
+ * Errors: JAC_EINVAL (k < 0), JAC_ETIMEOUT, JAC_ENUMERIC, JAC_ECUDA.
+ */
+jac_status jac_sweep(jac_ctx* ctx, int32_t k, double* relres_out);
+
+/*
+ * jac_solve -- iterate until the test value of the current iterate x^k is
+ * <= tol, or k reaches maxit (Algorithm 1's "loop until convergence", the
+ * test made before the update).
+ *   sweeps_out  (may be NULL) k, the number of updates applied since x^0
+ *               (the paper's iteration count is k+1).
+ *   relres_out  (may be NULL) the test value of x^k.
+ * JAC_FP64: every sweep is FP64.  JAC_MIXED: FP64 residual r = b - A x with
+ * the test, then inner_sweeps FP32 Jacobi sweeps on A e = r from e = 0,
+ * x += e; the test is made only at refinement steps, so k is a multiple of
+ * inner_sweeps.  Returns JAC_OK on convergence, JAC_ENOTCONV when maxit was
+ * reached (x valid), JAC_ENUMERIC on NaN/Inf, JAC_ETIMEOUT, JAC_ECUDA.
+ * Batched contexts stop every system separately; JAC_OK only if all converged.
+ */
+jac_status jac_solve(jac_ctx* ctx, double tol, int64_t maxit, int64_t* sweeps_out,
+                     double* relres_out);
+
+/* jac_get_x -- copy the current iterate x^k (n*nrhs, row-major, ORIGINAL row
+ * order) to `x` in `memory`. */
+jac_status jac_get_x(jac_ctx* ctx, double* x, int32_t memory);
+
+/* jac_get_history -- relres of the iterates evaluated by the last jac_sweep /
+ * jac_solve (first entry: the first iterate that call evaluated), when
+ * jac_opts.history > 0.  *count receives the number written (<= max). */
+jac_status jac_get_history(jac_ctx* ctx, double* out, int64_t max, int64_t* count);
+
+/* jac_get_batch_results -- per system s and right-hand side c (index s*nrhs+c):
+ * sweeps applied and the test value of the final iterate.  Host arrays. */
+jac_status jac_get_batch_results(jac_ctx* ctx, int64_t* sweeps, double* relres);
+
+/*
+ * jac_adjoint_grad -- gradients of a loss through x = A^{-1} b.
+ *
+ * Given the adjoint solution lambda = A^{-T} dL/dx (obtained from a context
+ * built with opts.transpose = 1) and the solution x, writes
+ *   dA[e] = -lambda_i * x_j   for every stored entry e = (i, j) of A, in the
+ *                             caller's CSR order (the pattern only), and
+ * leaves dL/db = lambda to the caller.  lambda, x: n doubles in the original
+ * row order, dA: nnz doubles, all in `memory`.  ctx is the forward context
+ * (its stored copy of A's pattern is used).  nrhs must be 1.
+ */
+jac_status jac_adjoint_grad(jac_ctx* ctx, const double* lambda, const double* x, double* dA,
+                            int32_t memory);
+
+/* jac_stats -- counters of the context (see jac_stats_t). */
+jac_status jac_stats(jac_ctx* ctx, jac_stats_t* out);
+
+/*
+ * jac_partition_plan -- host-only: the row permutation and partition row
+ * ranges jac_setup would use (Sec. 4.2-4.3), without a GPU.
+ *   perm      n entries: perm[new] = original row (0-based).
+ *   part_ptr  nparts_out+1 entries (caller allocates nparts+2 for SUBSTRUCT
+ *             = px*py*pz + 2, else nparts + 1): partition p owns new rows
+ *             [part_ptr[p], part_ptr[p+1]).
+ *   nparts_out (may be NULL) number of partitions.
+ * A must be in host memory.  Errors as jac_setup (without CUDA errors).
+ */
+jac_status jac_partition_plan(const jac_csr* A, jac_splitting s, int32_t nparts, const jac_opts* o,
+                              int64_t* perm, int64_t* part_ptr, int64_t* nparts_out);
+
+/*
+ * jac_dependency_lists -- host-only: the receive lists of the sparsity-pattern
+ * splitting (Sec. 4.2.2) for the partitions of jac_partition_plan.
+ * For partition p, the x entries (original 0-based indices) it receives,
+ * grouped by owner q ascending and sorted within a group:
+ *   recv_ptr  nparts+1 offsets into recv (partition p: [recv_ptr[p], recv_ptr[p+1]))
+ *   recv_from owner partition of each entry
+ *   recv      original index of each entry
+ * Call with recv == NULL first to get the total in *total (recv_ptr is
+ * still filled); then with arrays of that size.  The send lists are the
+ * receive lists read the other way round.
+ */
+jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t nparts, const jac_opts* o,
+                                int64_t* recv_ptr, int32_t* recv_from, int64_t* recv, int64_t* total);
+
+/* Message of the last failure on ctx (NULL ctx: last jac_setup* failure on
+ * this thread).  Never NULL; valid until the next call on ctx. */
+const char* jac_last_error(const jac_ctx* ctx);
+
+/* Release the context and everything it owns.  NULL-safe. */
+void jac_free(jac_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JACOBI_GB300_H */

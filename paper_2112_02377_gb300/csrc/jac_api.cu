@@ -1,0 +1,837 @@
+// C ABI of the GB300 Jacobi library: context life cycle, uploads, CUDA graphs
+// and the host loops around the sweep kernels.  See include/jacobi.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "jac_device.cuh"
+#include "jac_internal.h"
+#include "jac_launch.h"
+
+using namespace jac;
+
+static thread_local std::string g_setup_error = "no error";
+
+struct jac_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    jac_opts o{};
+    std::string err = "no error";
+    int64_t n = 0, nnz = 0, nnz_off = 0, max_row = 0, max_off = 0, halo_entries = 0, interface_rows = 0;
+    int nrhs = 1;
+    int splitting = 0, precision = 0, variant = 2;
+    int64_t nparts = 0;
+    // device data (new row order)
+    int* d_rowptr = nullptr;
+    int* d_col = nullptr;
+    double* d_T64 = nullptr;
+    float* d_T32 = nullptr;
+    double* d_c = nullptr;
+    double* d_d = nullptr;
+    double* d_x[2] = {nullptr, nullptr};
+    float* d_e[2] = {nullptr, nullptr};
+    float* d_dlt = nullptr;
+    Partial* d_part = nullptr;
+    int nslots = 0;
+    JacCtl* d_ctl = nullptr;
+    JacCtl* h_ctl = nullptr;     // pinned mirrors [2]
+    double* d_hist = nullptr;
+    int64_t hist_cap = 0;
+    long long* d_perm = nullptr;
+    double* d_stage = nullptr;   // n*nrhs staging (original order)
+    double* d_stage2 = nullptr;  // second staging buffer (adjoint)
+    double* d_grad = nullptr;    // nnz (adjoint)
+    int* d_orow = nullptr;       // original pattern (adjoint)
+    int* d_ocol = nullptr;
+    // tiling / launch
+    int* d_row0 = nullptr;
+    int* d_nnz0 = nullptr;
+    int* d_cta0 = nullptr;
+    int ntiles = 0, emax = 0, rows_per_tile = 256, stages = 4, grid = 0, threads = 0, smem = 0;
+    const void* pfn64 = nullptr;
+    const void* pfnmix = nullptr;
+    int K = 64;
+    cudaGraphExec_t g64 = nullptr, gmix = nullptr;
+    bool no_graph = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // host-side bookkeeping
+    int64_t sweeps_total = 0, outer_last = 0;
+    double last_ms = 0.0;
+    std::vector<long long> h_perm;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+jac_status fail(jac_ctx* c, jac_status st, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_setup_error = msg;
+    return st;
+}
+
+jac_status cuda_fail(jac_ctx* c, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? JAC_ENOMEM : JAC_ECUDA, m);
+}
+
+#define CK(ctx, call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);      \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemset(*p, 0, count * sizeof(T));
+}
+
+template <class T>
+void dfree(T*& p)
+{
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+cudaStream_t stream_of(const jac_ctx* c) { return c->stream; }
+
+jac_status copy_to_stage(jac_ctx* c, const double* src, int memory, size_t count, double* stage)
+{
+    if (memory == JAC_MEM_DEVICE) {
+        CK(c, cudaMemcpyAsync(stage, src, count * sizeof(double), cudaMemcpyDeviceToDevice, stream_of(c)));
+    } else if (memory == JAC_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(stage, src, count * sizeof(double), cudaMemcpyHostToDevice, stream_of(c)));
+    } else {
+        return fail(c, JAC_EINVAL, "memory must be JAC_MEM_HOST or JAC_MEM_DEVICE");
+    }
+    return JAC_OK;
+}
+
+double algorithmic_bytes_fp64(int64_t n, int64_t nnz_off)
+{
+    return 12.0 * nnz_off + 8.0 * n + 4.0 * (n + 1) + 8.0 * n + 8.0 * n + 8.0 * n;
+}
+
+double algorithmic_bytes_fp32(int64_t n, int64_t nnz_off)
+{
+    return 8.0 * nnz_off + 4.0 * (n + 1) + 4.0 * n + 4.0 * n + 4.0 * n;
+}
+
+DevMat devmat(const jac_ctx* c)
+{
+    DevMat m;
+    m.n = (int)c->n;
+    m.rowptr = c->d_rowptr;
+    m.col = c->d_col;
+    m.T64 = c->d_T64;
+    m.T32 = c->d_T32;
+    m.c = c->d_c;
+    m.d = c->d_d;
+    return m;
+}
+
+DevVec devvec(const jac_ctx* c)
+{
+    DevVec v;
+    v.x[0] = c->d_x[0];
+    v.x[1] = c->d_x[1];
+    v.e[0] = c->d_e[0];
+    v.e[1] = c->d_e[1];
+    v.dlt = c->d_dlt;
+    v.part = c->d_part;
+    v.nslots = c->nslots;
+    return v;
+}
+
+DevTiles devtiles(const jac_ctx* c)
+{
+    DevTiles t;
+    t.row0 = c->d_row0;
+    t.nnz0 = c->d_nnz0;
+    t.cta0 = c->d_cta0;
+    t.ntiles = c->ntiles;
+    t.emax = c->emax;
+    return t;
+}
+
+// Enqueue one "graph step": K sweeps (FP64) or one refinement cycle block (mixed).
+jac_status enqueue_step(jac_ctx* c, bool mixed)
+{
+    cudaStream_t s = stream_of(c);
+    if (c->variant == 2) {
+        CK(c, launch_reset_bar(c->d_ctl, s));
+        CK(c, launch_persistent(mixed ? c->pfnmix : c->pfn64, c->grid, c->threads, c->smem, devmat(c), devvec(c),
+                                devtiles(c), c->d_ctl, c->K, s));
+    } else {
+        if (!mixed) {
+            for (int i = 0; i < c->K; ++i) CK(c, launch_row_sweep(PH_P64, devmat(c), devvec(c), c->d_ctl, s));
+        } else {
+            const int m = c->o.inner_sweeps;
+            CK(c, launch_row_sweep(PH_P64R, devmat(c), devvec(c), c->d_ctl, s));
+            for (int j = 1; j < m - 1; ++j) CK(c, launch_row_sweep(PH_P32, devmat(c), devvec(c), c->d_ctl, s));
+            CK(c, launch_row_sweep(PH_P32L, devmat(c), devvec(c), c->d_ctl, s));
+        }
+    }
+    return JAC_OK;
+}
+
+jac_status get_graph(jac_ctx* c, bool mixed, cudaGraphExec_t* out)
+{
+    cudaGraphExec_t& g = mixed ? c->gmix : c->g64;
+    if (!g) {
+        cudaStream_t s = stream_of(c);
+        cudaStream_t cap = s;
+        bool own = false;
+        if (!s) {   // legacy stream cannot be captured: capture on a private stream
+            CK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            own = true;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaStream_t saved = c->stream;
+            c->stream = cap;
+            jac_status st = enqueue_step(c, mixed);
+            c->stream = saved;
+            cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+            if (st != JAC_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                if (own) cudaStreamDestroy(cap);
+                return st;
+            }
+            e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (own) cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            g = nullptr;
+            cudaGetLastError();
+            return cuda_fail(c, e, "CUDA graph capture of the sweep loop");
+        }
+    }
+    *out = g;
+    return JAC_OK;
+}
+
+jac_status run_graph(jac_ctx* c, bool mixed)
+{
+    if (c->no_graph) return enqueue_step(c, mixed);
+    cudaGraphExec_t g;
+    jac_status st = get_graph(c, mixed, &g);
+    if (st != JAC_OK) {
+        // Stream capture of this launch form is unavailable: launch directly.
+        c->no_graph = true;
+        cudaGetLastError();
+        return enqueue_step(c, mixed);
+    }
+    CK(c, cudaGraphLaunch(g, stream_of(c)));
+    return JAC_OK;
+}
+
+jac_status status_from_ctl(jac_ctx* c, const JacCtl& h)
+{
+    if (h.status & ST_TIMEOUT)
+        return fail(c, JAC_ETIMEOUT, "a device-side wait exceeded its bound (grid barrier or copy); iterate undefined");
+    if ((h.status & ST_NUMERIC) || h.done == DONE_NUMERIC)
+        return fail(c, JAC_ENUMERIC, "the residual became NaN or Inf (the iteration diverges)");
+    return JAC_OK;
+}
+
+jac_status arm(jac_ctx* c, int test, int mixed, long long k_limit, long long k_delta, double tol)
+{
+    CK(c, launch_arm(c->d_ctl, test, mixed, c->o.inner_sweeps, k_limit, k_delta, tol, c->o.norm, c->d_hist, c->hist_cap,
+                     (long long)c->o.timeout_cycles, c->o.fault_skip_cta, stream_of(c)));
+    return JAC_OK;
+}
+
+jac_status fetch_ctl(jac_ctx* c, JacCtl* dst)
+{
+    CK(c, cudaMemcpyAsync(dst, c->d_ctl, sizeof(JacCtl), cudaMemcpyDeviceToHost, stream_of(c)));
+    return JAC_OK;
+}
+
+void destroy(jac_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->g64) cudaGraphExecDestroy(c->g64);
+    if (c->gmix) cudaGraphExecDestroy(c->gmix);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    dfree(c->d_rowptr); dfree(c->d_col); dfree(c->d_T64); dfree(c->d_T32); dfree(c->d_c); dfree(c->d_d);
+    dfree(c->d_x[0]); dfree(c->d_x[1]); dfree(c->d_e[0]); dfree(c->d_e[1]); dfree(c->d_dlt);
+    dfree(c->d_part); dfree(c->d_ctl); dfree(c->d_hist); dfree(c->d_perm); dfree(c->d_stage); dfree(c->d_stage2);
+    dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0); dfree(c->d_cta0);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    delete c;
+}
+
+// Host copy of a caller CSR that may live in device memory.
+struct HostView {
+    std::vector<int32_t> rp, cl;
+    std::vector<double> vl;
+    jac_csr csr{};
+};
+
+jac_status host_view(const jac_csr* A, HostView& hv, jac_ctx* err_ctx)
+{
+    if (!A) return fail(err_ctx, JAC_EINVAL, "A is NULL");
+    if (A->memory == JAC_MEM_HOST) {
+        hv.csr = *A;
+        return JAC_OK;
+    }
+    if (A->memory != JAC_MEM_DEVICE) return fail(err_ctx, JAC_EINVAL, "A->memory must be HOST or DEVICE");
+    if (A->n < 1 || A->nnz < 0) return fail(err_ctx, JAC_EINVAL, "bad n / nnz");
+    hv.rp.resize(A->n + 1);
+    hv.cl.resize(A->nnz);
+    hv.vl.resize(A->nnz);
+    cudaError_t e = cudaMemcpy(hv.rp.data(), A->rowptr, (A->n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && A->nnz)
+        e = cudaMemcpy(hv.cl.data(), A->col, A->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && A->nnz)
+        e = cudaMemcpy(hv.vl.data(), A->val, A->nnz * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(err_ctx, e, "copy of the device CSR to the host");
+    hv.csr = *A;
+    hv.csr.rowptr = hv.rp.data();
+    hv.csr.col = hv.cl.data();
+    hv.csr.val = hv.vl.data();
+    hv.csr.memory = JAC_MEM_HOST;
+    return JAC_OK;
+}
+
+jac_status check_opts(const jac_opts& o, jac_ctx* err_ctx)
+{
+    if (o.precision != JAC_FP64 && o.precision != JAC_MIXED) return fail(err_ctx, JAC_EINVAL, "opts.precision");
+    if (o.norm != JAC_NORM_REL2 && o.norm != JAC_NORM_INF) return fail(err_ctx, JAC_EINVAL, "opts.norm must be 2 or 0");
+    if (o.sweeps_per_graph < 1 || o.sweeps_per_graph > 4096) return fail(err_ctx, JAC_EINVAL, "opts.sweeps_per_graph");
+    if (o.inner_sweeps < 2 || o.inner_sweeps > 100000)
+        return fail(err_ctx, JAC_EINVAL, "opts.inner_sweeps must be in [2, 100000]");
+    if (o.nrhs != 1) return fail(err_ctx, JAC_EINVAL, "opts.nrhs > 1 is supported by jac_setup_batched only");
+    if (o.variant < 0 || o.variant > 2) return fail(err_ctx, JAC_EINVAL, "opts.variant must be 0, 1 or 2");
+    if (o.tile_rows != 0 && o.tile_rows != 256 && o.tile_rows != 512)
+        return fail(err_ctx, JAC_EINVAL, "opts.tile_rows must be 0, 256 or 512");
+    if (o.history < 0) return fail(err_ctx, JAC_EINVAL, "opts.history must be >= 0");
+    return JAC_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+void jac_opts_default(jac_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = JAC_FP64;
+    o->norm = JAC_NORM_REL2;
+    o->sweeps_per_graph = 64;
+    o->inner_sweeps = 128;
+    o->nrhs = 1;
+    o->transpose = 0;
+    o->variant = 0;
+    o->tile_rows = 0;
+    o->history = 0;
+    o->stream = nullptr;
+    o->timeout_cycles = 0;
+    o->fault_skip_cta = -1;
+    o->device = -1;
+}
+
+const char* jac_last_error(const jac_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_setup_error.c_str();
+}
+
+void jac_free(jac_ctx* ctx) { destroy(ctx); }
+
+jac_status jac_partition_plan(const jac_csr* A, jac_splitting s, int32_t nparts, const jac_opts* o_in,
+                              int64_t* perm, int64_t* part_ptr, int64_t* nparts_out)
+{
+    jac_opts o;
+    jac_opts_default(&o);
+    if (o_in) o = *o_in;
+    if (!A || A->memory != JAC_MEM_HOST) return fail(nullptr, JAC_EINVAL, "A must be in host memory");
+    if (!perm || !part_ptr) return fail(nullptr, JAC_EINVAL, "perm / part_ptr are NULL");
+    HostCSR M;
+    Error e = host_csr_from_abi(A, o.transpose != 0, M);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    Plan plan;
+    e = make_plan(M, s, nparts, o, plan);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    for (int64_t r = 0; r < M.n; ++r) perm[r] = plan.perm[r];
+    for (int64_t p = 0; p <= plan.nparts(); ++p) part_ptr[p] = plan.part_ptr[p];
+    if (nparts_out) *nparts_out = plan.nparts();
+    return JAC_OK;
+}
+
+jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t nparts, const jac_opts* o_in,
+                                int64_t* recv_ptr, int32_t* recv_from, int64_t* recv, int64_t* total)
+{
+    jac_opts o;
+    jac_opts_default(&o);
+    if (o_in) o = *o_in;
+    if (!A || A->memory != JAC_MEM_HOST) return fail(nullptr, JAC_EINVAL, "A must be in host memory");
+    if (!recv_ptr || !total) return fail(nullptr, JAC_EINVAL, "recv_ptr / total are NULL");
+    HostCSR M;
+    Error e = host_csr_from_abi(A, o.transpose != 0, M);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    Plan plan;
+    e = make_plan(M, s, nparts, o, plan);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    std::vector<int64_t> rp, rc;
+    std::vector<int32_t> rf;
+    dependency_lists(M, plan, rp, rf, rc);
+    for (size_t p = 0; p < rp.size(); ++p) recv_ptr[p] = rp[p];
+    if (recv) {
+        if (*total < (int64_t)rc.size()) return fail(nullptr, JAC_EINVAL, "recv arrays too small");
+        for (size_t q = 0; q < rc.size(); ++q) { recv[q] = rc[q]; if (recv_from) recv_from[q] = rf[q]; }
+    }
+    *total = (int64_t)rc.size();
+    return JAC_OK;
+}
+
+jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, const jac_opts* o_in,
+                     jac_ctx** out)
+{
+    if (!out) return fail(nullptr, JAC_EINVAL, "out is NULL");
+    *out = nullptr;
+    jac_opts o;
+    jac_opts_default(&o);
+    if (o_in) o = *o_in;
+    if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
+    jac_status st = check_opts(o, nullptr);
+    if (st != JAC_OK) return st;
+    int dev = o.device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, JAC_ECUDA, "no CUDA device");
+    }
+    DeviceGuard guard(dev);
+    HostView hv;
+    st = host_view(A, hv, nullptr);
+    if (st != JAC_OK) return st;
+    HostCSR M;
+    Error e = host_csr_from_abi(&hv.csr, o.transpose != 0, M);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    Plan plan;
+    e = make_plan(M, s, nparts, o, plan);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    TForm tf;
+    e = make_tform(M, plan, tf);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+
+    std::unique_ptr<jac_ctx, void (*)(jac_ctx*)> c(new jac_ctx(), destroy);
+    c->device = dev;
+    c->stream = (cudaStream_t)o.stream;
+    c->o = o;
+    c->n = M.n;
+    c->nnz = M.nnz();
+    c->nnz_off = tf.rowptr[M.n];
+    c->max_off = tf.max_off;
+    c->max_row = tf.max_off + 1;
+    c->splitting = s;
+    c->precision = o.precision;
+    c->nparts = plan.nparts();
+    c->interface_rows = plan.interface_rows;
+    c->K = o.sweeps_per_graph;
+    {
+        std::vector<int64_t> rp, rc;
+        std::vector<int32_t> rf;
+        dependency_lists(M, plan, rp, rf, rc);
+        c->halo_entries = (int64_t)rc.size();
+    }
+    jac_ctx* C = c.get();
+    const int64_t n = M.n, nnz_off = c->nnz_off;
+    if (n > INT32_MAX - 64) return fail(nullptr, JAC_EINVAL, "n too large");
+
+    // ---- launch configuration
+    cudaDeviceProp prop;
+    CK(nullptr, cudaGetDeviceProperties(&prop, dev));
+    c->variant = o.variant == 0 ? 2 : o.variant;
+    c->rows_per_tile = o.tile_rows ? o.tile_rows : 256;
+    c->stages = 4;
+    if (c->variant == 2) {
+        const int rows = c->rows_per_tile;
+        // Stage budget: 2 CTAs/SM x 4 stages for 256-row tiles, 1 CTA/SM x 4
+        // stages for 512-row tiles (~220 KB of shared memory per SM).
+        const int64_t stage_budget = rows == 256 ? 26 * 1024 : 52 * 1024;
+        int64_t cap_entries = (int64_t)std::max<int64_t>(1, tf.max_off) * rows;
+        const int64_t budget_entries = std::max<int64_t>(rows, (stage_budget - 24 * rows - 1024) / 12);
+        c->emax = (int)std::min<int64_t>(cap_entries, budget_entries);
+        c->pfn64 = persistent_kernel(rows, c->stages, false);
+        c->pfnmix = persistent_kernel(rows, c->stages, true);
+        c->smem = persistent_smem_bytes(rows, c->emax, c->stages);
+        c->threads = 256 + 32;
+        int per_sm = 0;
+        if (c->pfn64 && c->pfnmix) {
+            CK(nullptr, cudaFuncSetAttribute(c->pfn64, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
+            CK(nullptr, cudaFuncSetAttribute(c->pfnmix, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
+            int a = 0, b2 = 0;
+            CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, c->pfn64, c->threads, c->smem));
+            CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, c->pfnmix, c->threads, c->smem));
+            per_sm = std::min(std::min(a, b2), 2);
+        }
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (per_sm < 1 || !coop) {
+            if (o.variant == 2) {
+                char msg[200];
+                std::snprintf(msg, sizeof(msg),
+                              "persistent kernel cannot be made co-resident (rows %d, smem %d B, %d CTAs/SM, coop %d)",
+                              rows, c->smem, per_sm, coop);
+                return fail(nullptr, JAC_EINVAL, msg);
+            }
+            c->variant = 1;
+        } else {
+            c->grid = per_sm * prop.multiProcessorCount;
+        }
+    }
+    if (c->variant == 1) {
+        c->grid = (int)((n + 255) / 256);
+        c->emax = 0;
+    }
+    Tiling tl;
+    if (c->variant == 2) {
+        make_tiling(tf, plan, c->rows_per_tile, c->emax, c->grid, tl);
+        c->ntiles = (int)tl.ntiles();
+    }
+    c->nslots = c->grid;
+
+    // ---- device buffers
+    CK(nullptr, dalloc(&c->d_rowptr, n + 1 + 16));
+    CK(nullptr, dalloc(&c->d_col, nnz_off + 16));
+    CK(nullptr, dalloc(&c->d_T64, nnz_off + 16));
+    CK(nullptr, dalloc(&c->d_c, n + 16));
+    CK(nullptr, dalloc(&c->d_d, n + 16));
+    CK(nullptr, dalloc(&c->d_x[0], n + 16));
+    CK(nullptr, dalloc(&c->d_x[1], n + 16));
+    if (o.precision == JAC_MIXED) {
+        CK(nullptr, dalloc(&c->d_T32, nnz_off + 16));
+        CK(nullptr, dalloc(&c->d_e[0], n + 16));
+        CK(nullptr, dalloc(&c->d_e[1], n + 16));
+        CK(nullptr, dalloc(&c->d_dlt, n + 16));
+    }
+    CK(nullptr, dalloc(&c->d_part, 2 * (size_t)c->nslots + 2));
+    CK(nullptr, dalloc(&c->d_ctl, 1));
+    CK(nullptr, dalloc(&c->d_perm, n));
+    CK(nullptr, dalloc(&c->d_stage, n + 16));
+    CK(nullptr, cudaMallocHost((void**)&c->h_ctl, 2 * sizeof(JacCtl)));
+    std::memset(c->h_ctl, 0, 2 * sizeof(JacCtl));
+    if (o.history > 0) {
+        c->hist_cap = o.history;
+        CK(nullptr, dalloc(&c->d_hist, c->hist_cap));
+    }
+    CK(nullptr, cudaEventCreate(&c->ev0));
+    CK(nullptr, cudaEventCreate(&c->ev1));
+    if (c->variant == 2) {
+        CK(nullptr, dalloc(&c->d_row0, tl.row0.size()));
+        CK(nullptr, dalloc(&c->d_nnz0, tl.nnz0.size()));
+        CK(nullptr, dalloc(&c->d_cta0, tl.cta0.size()));
+        CK(nullptr, cudaMemcpy(c->d_row0, tl.row0.data(), tl.row0.size() * 4, cudaMemcpyHostToDevice));
+        CK(nullptr, cudaMemcpy(c->d_nnz0, tl.nnz0.data(), tl.nnz0.size() * 4, cudaMemcpyHostToDevice));
+        CK(nullptr, cudaMemcpy(c->d_cta0, tl.cta0.data(), tl.cta0.size() * 4, cudaMemcpyHostToDevice));
+    }
+    CK(nullptr, cudaMemcpy(c->d_rowptr, tf.rowptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
+    if (nnz_off) {
+        CK(nullptr, cudaMemcpy(c->d_col, tf.col.data(), nnz_off * 4, cudaMemcpyHostToDevice));
+        CK(nullptr, cudaMemcpy(c->d_T64, tf.T.data(), nnz_off * 8, cudaMemcpyHostToDevice));
+        if (o.precision == JAC_MIXED) {
+            std::vector<float> t32(nnz_off);
+            for (int64_t k = 0; k < nnz_off; ++k) t32[k] = (float)tf.T[k];
+            CK(nullptr, cudaMemcpy(c->d_T32, t32.data(), nnz_off * 4, cudaMemcpyHostToDevice));
+        }
+    }
+    CK(nullptr, cudaMemcpy(c->d_d, tf.d.data(), n * 8, cudaMemcpyHostToDevice));
+    c->h_perm.assign(plan.perm.begin(), plan.perm.end());
+    CK(nullptr, cudaMemcpy(c->d_perm, c->h_perm.data(), n * sizeof(long long), cudaMemcpyHostToDevice));
+    // original pattern for the adjoint gradient (forward contexts)
+    if (!o.transpose) {
+        HostCSR P;
+        Error e2 = host_csr_from_abi(&hv.csr, false, P);
+        if (!e2.ok()) return fail(nullptr, e2.st, e2.msg);
+        CK(nullptr, dalloc(&c->d_orow, n + 1));
+        CK(nullptr, dalloc(&c->d_ocol, (size_t)P.nnz()));
+        CK(nullptr, cudaMemcpy(c->d_orow, P.rowptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
+        if (P.nnz()) CK(nullptr, cudaMemcpy(c->d_ocol, P.col.data(), P.nnz() * 4, cudaMemcpyHostToDevice));
+    }
+    // right-hand side and control block
+    cudaStream_t sm = stream_of(C);
+    if (b) {
+        st = copy_to_stage(C, b, A->memory, (size_t)n, c->d_stage);
+        if (st != JAC_OK) return fail(nullptr, st, C->err);
+    }
+    CK(nullptr, launch_make_c(c->d_perm, b ? c->d_stage : nullptr, c->d_d, c->d_c, (int)n, c->d_ctl, sm));
+    CK(nullptr, launch_reset_iterate(c->d_ctl, sm));
+    CK(nullptr, launch_arm(c->d_ctl, 0, 0, o.inner_sweeps, 0, 0, -1.0, o.norm, c->d_hist, c->hist_cap, (long long)o.timeout_cycles,
+                     o.fault_skip_cta, sm));
+    if (fetch_ctl(C, &c->h_ctl[0]) != JAC_OK) return fail(nullptr, JAC_ECUDA, C->err);
+    CK(nullptr, sm ? cudaStreamSynchronize(sm) : cudaDeviceSynchronize());
+    *out = c.release();
+    return JAC_OK;
+}
+
+jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const* b, const jac_opts* o,
+                             jac_ctx** out)
+{
+    (void)nsys; (void)A; (void)b; (void)o;
+    if (out) *out = nullptr;
+    return fail(nullptr, JAC_EINVAL, "jac_setup_batched: not available in this build");
+}
+
+jac_status jac_set_x(jac_ctx* c, const double* x, int32_t memory)
+{
+    if (!c) return JAC_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream_of(c);
+    if (x) {
+        jac_status st = copy_to_stage(c, x, memory, (size_t)c->n, c->d_stage);
+        if (st != JAC_OK) return st;
+    }
+    CK(c, launch_gather_rows(c->d_perm, x ? c->d_stage : nullptr, c->d_x[0], (int)c->n, 1, s));
+    CK(c, launch_reset_iterate(c->d_ctl, s));
+    if (fetch_ctl(c, &c->h_ctl[0]) != JAC_OK) return JAC_ECUDA;
+    CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
+    c->sweeps_total = 0;
+    return JAC_OK;
+}
+
+jac_status jac_set_b(jac_ctx* c, const double* b, int32_t memory)
+{
+    if (!c) return JAC_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream_of(c);
+    if (b) {
+        jac_status st = copy_to_stage(c, b, memory, (size_t)c->n, c->d_stage);
+        if (st != JAC_OK) return st;
+    }
+    CK(c, launch_make_c(c->d_perm, b ? c->d_stage : nullptr, c->d_d, c->d_c, (int)c->n, c->d_ctl, s));
+    CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
+    return JAC_OK;
+}
+
+jac_status jac_sweep(jac_ctx* c, int32_t k, double* relres_out)
+{
+    if (!c) return JAC_EINVAL;
+    if (k < 0) return fail(c, JAC_EINVAL, "k must be >= 0");
+    if (k == 0) {
+        if (relres_out) *relres_out = c->h_ctl[0].relres;
+        return JAC_OK;
+    }
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream_of(c);
+    jac_status st = arm(c, 0, 0, 0, k, -1.0);
+    if (st != JAC_OK) return st;
+    const int launches = (k + c->K - 1) / c->K;
+    CK(c, cudaEventRecord(c->ev0, s));
+    for (int i = 0; i < launches; ++i) {
+        st = run_graph(c, false);
+        if (st != JAC_OK) return st;
+    }
+    CK(c, cudaEventRecord(c->ev1, s));
+    st = fetch_ctl(c, &c->h_ctl[0]);
+    if (st != JAC_OK) return st;
+    CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    c->last_ms = ms;
+    const JacCtl& h = c->h_ctl[0];
+    st = status_from_ctl(c, h);
+    if (st != JAC_OK) return st;
+    c->sweeps_total += h.evals;
+    if (relres_out) *relres_out = h.relres;
+    return JAC_OK;
+}
+
+jac_status jac_solve(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out, double* relres_out)
+{
+    if (!c) return JAC_EINVAL;
+    if (maxit < 0) return fail(c, JAC_EINVAL, "maxit must be >= 0");
+    if (!(tol >= 0.0)) return fail(c, JAC_EINVAL, "tol must be >= 0");
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream_of(c);
+    const bool mixed = (c->precision == JAC_MIXED);
+    jac_status st = arm(c, 1, mixed ? 1 : 0, maxit, -1, tol);
+    if (st != JAC_OK) return st;
+    CK(c, cudaEventRecord(c->ev0, s));
+    // Launch graph steps, keeping one step in flight while the previous
+    // step's control block is inspected on the host.
+    JacCtl* ha = &c->h_ctl[0];
+    JacCtl* hb = &c->h_ctl[1];
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    CK(c, cudaEventCreateWithFlags(&ea, cudaEventDisableTiming));
+    CK(c, cudaEventCreateWithFlags(&eb, cudaEventDisableTiming));
+    auto cleanup = [&]() { cudaEventDestroy(ea); cudaEventDestroy(eb); };
+    st = run_graph(c, mixed);
+    if (st == JAC_OK) st = fetch_ctl(c, ha);
+    if (st != JAC_OK) { cleanup(); return st; }
+    cudaEventRecord(ea, s);
+    long long last_k = -1;
+    int stalled = 0;
+    // Every step runs K sweeps unless the solve is over, so a finished solve
+    // needs at most (maxit + inner + 1) / K + 2 steps; more means a defect.
+    const long long per_step = (c->variant == 1 && mixed) ? c->o.inner_sweeps : c->K;
+    const long long step_cap = (maxit + (long long)c->o.inner_sweeps + 1) / per_step + 4;
+    long long steps = 1;
+    for (;;) {
+        if (++steps > step_cap) {
+            cudaStreamSynchronize(s);
+            cleanup();
+            return fail(c, JAC_ECUDA, "the sweep loop did not terminate within its step bound");
+        }
+        st = run_graph(c, mixed);
+        if (st == JAC_OK) st = fetch_ctl(c, hb);
+        if (st != JAC_OK) { cleanup(); return st; }
+        cudaEventRecord(eb, s);
+        cudaError_t e = cudaEventSynchronize(ea);
+        if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "solve loop"); }
+        if (ha->done != DONE_RUNNING || ha->status != 0) break;
+        const long long prog = ha->k * 4 + ha->phase + ha->evals;
+        if (prog == last_k) {
+            if (++stalled > 4) {
+                cudaStreamSynchronize(s);
+                cleanup();
+                return fail(c, JAC_ECUDA, "the sweep loop made no progress");
+            }
+        } else {
+            stalled = 0;
+        }
+        last_k = prog;
+        std::swap(ha, hb);
+        std::swap(ea, eb);
+    }
+    CK(c, cudaEventRecord(c->ev1, s));
+    cudaError_t e = cudaEventSynchronize(eb);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(c, e, "solve loop");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    c->last_ms = ms;
+    // the later copy (hb) holds the final state; keep it in slot 0
+    c->h_ctl[0] = *hb;
+    const JacCtl& h = c->h_ctl[0];
+    st = status_from_ctl(c, h);
+    if (st != JAC_OK) return st;
+    c->sweeps_total = h.k;
+    c->outer_last = h.outer;
+    if (sweeps_out) *sweeps_out = h.k;
+    if (relres_out) *relres_out = h.relres;
+    if (h.done == DONE_LIMIT) return fail(c, JAC_ENOTCONV, "maxit reached before the tolerance");
+    if (h.done != DONE_CONVERGED) return fail(c, JAC_ECUDA, "solve ended in an unexpected state");
+    return JAC_OK;
+}
+
+jac_status jac_get_x(jac_ctx* c, double* x, int32_t memory)
+{
+    if (!c || !x) return c ? fail(c, JAC_EINVAL, "x is NULL") : JAC_EINVAL;
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream_of(c);
+    const int xb = c->h_ctl[0].xbuf & 1;
+    CK(c, launch_scatter_rows(c->d_perm, c->d_x[xb], c->d_stage, (int)c->n, 1, s));
+    if (memory == JAC_MEM_DEVICE) {
+        CK(c, cudaMemcpyAsync(x, c->d_stage, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else if (memory == JAC_MEM_HOST) {
+        CK(c, cudaMemcpyAsync(x, c->d_stage, c->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    } else {
+        return fail(c, JAC_EINVAL, "memory must be JAC_MEM_HOST or JAC_MEM_DEVICE");
+    }
+    CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
+    return JAC_OK;
+}
+
+jac_status jac_get_history(jac_ctx* c, double* out, int64_t max, int64_t* count)
+{
+    if (!c || !count) return JAC_EINVAL;
+    const int64_t have = std::min<int64_t>(c->h_ctl[0].evals, c->hist_cap);
+    const int64_t m = std::min<int64_t>(have, std::max<int64_t>(max, 0));
+    if (m > 0 && out) {
+        DeviceGuard g(c->device);
+        CK(c, cudaMemcpy(out, c->d_hist, m * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    *count = out ? m : have;
+    return JAC_OK;
+}
+
+jac_status jac_get_batch_results(jac_ctx* c, int64_t* sweeps, double* relres)
+{
+    if (!c) return JAC_EINVAL;
+    if (sweeps) sweeps[0] = c->h_ctl[0].k;
+    if (relres) relres[0] = c->h_ctl[0].relres;
+    return JAC_OK;
+}
+
+jac_status jac_adjoint_grad(jac_ctx* c, const double* lambda, const double* x, double* dA, int32_t memory)
+{
+    if (!c || !lambda || !x || !dA) return c ? fail(c, JAC_EINVAL, "NULL argument") : JAC_EINVAL;
+    if (!c->d_orow) return fail(c, JAC_EINVAL, "jac_adjoint_grad needs the forward (non-transposed) context");
+    DeviceGuard g(c->device);
+    cudaStream_t s = stream_of(c);
+    if (!c->d_stage2) CK(c, dalloc(&c->d_stage2, c->n + 16));
+    if (!c->d_grad) CK(c, dalloc(&c->d_grad, (size_t)c->nnz + 16));
+    jac_status st = copy_to_stage(c, lambda, memory, (size_t)c->n, c->d_stage);
+    if (st != JAC_OK) return st;
+    st = copy_to_stage(c, x, memory, (size_t)c->n, c->d_stage2);
+    if (st != JAC_OK) return st;
+    CK(c, launch_adjoint_grad(c->d_orow, c->d_ocol, c->d_stage, c->d_stage2, c->d_grad, (int)c->n, s));
+    CK(c, cudaMemcpyAsync(dA, c->d_grad, c->nnz * sizeof(double),
+                          memory == JAC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
+    return JAC_OK;
+}
+
+jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
+{
+    if (!c || !out) return JAC_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    const JacCtl& h = c->h_ctl[0];
+    out->n = c->n;
+    out->nnz = c->nnz;
+    out->nparts = c->nparts;
+    out->interface_rows = c->interface_rows;
+    out->ntiles = c->ntiles;
+    out->ctas = c->grid;
+    out->halo_entries = c->halo_entries;
+    out->max_row = c->max_row;
+    out->k = h.k;
+    out->sweeps_total = c->sweeps_total;
+    out->outer_iterations = c->outer_last;
+    out->last_relres = h.relres;
+    out->last_res2 = h.res2;
+    out->last_resinf = h.resinf;
+    out->last_ms = c->last_ms;
+    out->bytes_per_sweep_fp64 = algorithmic_bytes_fp64(c->n, c->nnz_off);
+    out->bytes_per_sweep_fp32 = algorithmic_bytes_fp32(c->n, c->nnz_off);
+    out->variant = c->variant;
+    out->precision = c->precision;
+    out->splitting = c->splitting;
+    out->nrhs = c->nrhs;
+    return JAC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+// Device-side state, helpers and the residual-norm bookkeeping shared by the
+// sweep kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace jac {
+
+// Status bits written by kernels into JacCtl::status.
+enum : int { ST_TIMEOUT = 1, ST_NUMERIC = 2 };
+// JacCtl::done values.
+enum : int { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_LIMIT = 2, DONE_NUMERIC = 3 };
+// Sweep phases.  P64: plain FP64 Jacobi sweep.  P64R: FP64 residual pass of
+// the mixed refinement (writes delta = D^{-1} r, no update of x).  P32: FP32
+// inner sweep e' = delta + T e.  P32L: last inner sweep, fused x += e.
+enum : int { PH_P64 = 0, PH_P64R = 1, PH_P32 = 2, PH_P32L = 3 };
+
+// Control block in device memory.  Kernels read it at start and the last /
+// first CTA writes it back; the host arms it before each call.
+struct JacCtl {
+    unsigned long long bar;   // grid-barrier arrivals of the current launch
+    unsigned int ticket;      // last-block detection of the per-sweep launch kernel
+    int status;               // ST_* bits
+    int done;                 // DONE_*
+    int test;                 // 1 = convergence test armed
+    int mixed;                // 1 = refinement cycle (P64R, P32.., P32L)
+    int phase;                // mixed: position in the cycle, 0 = P64R
+    int inner;                // mixed: sweeps per cycle m (>= 2)
+    int xbuf;                 // which x buffer holds the current iterate
+    int norm_kind;            // 2 = relative 2-norm, 0 = absolute inf-norm
+    int fault_skip_cta;       // test hook, -1 = off
+    long long k;              // index of the current iterate x^k
+    long long k_limit;        // sweep mode: stop when k == k_limit; test mode: last iterate to evaluate
+    long long evals;          // residual evaluations in the current call
+    long long outer;          // mixed: refinement steps in the current call
+    long long k_eval;         // iterate whose residual is in relres
+    long long timeout;        // clock64 budget of one wait
+    double tol;
+    double bnorm;             // ||b||_2
+    double relres, res2, resinf;
+    double* hist;             // optional history (device), hist_cap entries
+    long long hist_cap;
+};
+
+struct Partial {
+    double ss;                // sum of r_i^2
+    unsigned long long mx;    // max |r_i| as IEEE bits (order-preserving for |r|)
+};
+
+// Off-diagonal iteration-matrix data in the new row order (constant during a solve).
+struct DevMat {
+    int n;
+    const int* rowptr;        // n+1 (+pad)
+    const int* col;           // nnz_off (+pad)
+    const double* T64;        // nnz_off (+pad)
+    const float* T32;         // nnz_off (+pad), mixed only
+    const double* c;          // n (+pad): b_i / a_ii
+    const double* d;          // n (+pad): a_ii
+};
+
+struct DevVec {
+    double* x[2];             // FP64 iterate, ping-pong
+    float* e[2];              // FP32 inner iterate, ping-pong (mixed)
+    float* dlt;               // FP32 delta = D^{-1} r (mixed)
+    Partial* part;            // [2][nslots] per-sweep partial norms
+    int nslots;
+};
+
+struct DevTiles {
+    const int* row0;          // ntiles+1
+    const int* nnz0;          // ntiles+1
+    const int* cta0;          // ctas+1
+    int ntiles;
+    int emax;                 // staged entry cap of a tile
+};
+
+__device__ __forceinline__ unsigned long long abs_bits(double r)
+{
+    return (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
+}
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b)
+{
+    return a > b ? a : b;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;   // valid in lane 0
+}
+
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v)
+{
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Fixed-order reduction of `cnt` partials by one warp (lane 0 gets the result).
+__device__ __forceinline__ void reduce_partials_warp(const Partial* p, int cnt, double& ss,
+                                                     unsigned long long& mx)
+{
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    unsigned long long m = 0;
+    for (int i = lane; i < cnt; i += 32) {
+        s += __ldcg(&p[i].ss);
+        m = umax64(m, __ldcg(&p[i].mx));
+    }
+    s = warp_sum(s);
+    m = warp_max(m);
+    ss = __shfl_sync(0xffffffffu, s, 0);
+    mx = __shfl_sync(0xffffffffu, m, 0);
+}
+
+// Test value and next state after evaluating the residual of iterate k.
+// Pure function of its inputs: every CTA computing it from the same partial
+// sums takes the same decision.
+struct Decision {
+    double relres, res2, resinf;
+    int done;         // DONE_*
+    bool numeric_bad;
+};
+
+__device__ __forceinline__ Decision decide(int test, double tol, long long k_limit, int norm_kind, double bnorm,
+                                          double ss, unsigned long long mx, long long k)
+{
+    Decision d;
+    d.res2 = sqrt(ss);
+    d.resinf = __longlong_as_double((long long)mx);
+    d.relres = (norm_kind == 2) ? (bnorm > 0.0 ? d.res2 / bnorm : d.res2) : d.resinf;
+    d.numeric_bad = !(ss <= 1.7976931348623157e308) || mx >= 0x7ff0000000000000ull;
+    if (d.numeric_bad) d.done = DONE_NUMERIC;
+    else if (test && d.relres <= tol) d.done = DONE_CONVERGED;
+    else if (test && k >= k_limit) d.done = DONE_LIMIT;
+    else d.done = DONE_RUNNING;
+    return d;
+}
+
+// ---------------------------------------------------------------- PTX ------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 1-D bulk copy global -> shared, completion counted on `bar` (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar,
+                                         uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p)
+{
+    return *(volatile const int*)p;
+}
+
+}  // namespace jac

@@ -1,0 +1,74 @@
+// Internal declarations of the GB300 Jacobi library (host side).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/jacobi.h"
+
+namespace jac {
+
+// A square matrix in 0-based CSR, host memory.
+struct HostCSR {
+    int64_t n = 0;
+    std::vector<int32_t> rowptr;   // n+1
+    std::vector<int32_t> col;      // nnz
+    std::vector<double> val;       // nnz
+    int64_t nnz() const { return rowptr.empty() ? 0 : rowptr.back(); }
+};
+
+// Row permutation and partition ranges of a splitting (paper Sec. 4).
+struct Plan {
+    int32_t splitting = JAC_BANDROW;
+    std::vector<int64_t> perm;      // perm[new] = original row
+    std::vector<int64_t> iperm;     // iperm[original] = new row
+    std::vector<int64_t> part_ptr;  // partition p owns new rows [part_ptr[p], part_ptr[p+1])
+    int64_t interface_rows = 0;     // SUBSTRUCT only
+    int64_t nparts() const { return (int64_t)part_ptr.size() - 1; }
+};
+
+// Off-diagonal part of P A P^T in the iteration-matrix form of Sec. 3:
+//   x'_i = c_i + sum_j T_ij x_j,  T_ij = -a_ij / a_ii,  c_i = b_i / a_ii,
+// rows in the new order, each row's entries in the ORIGINAL stored order with
+// columns renumbered to the new order.  d_i = a_ii.
+struct TForm {
+    int64_t n = 0;
+    std::vector<int32_t> rowptr;    // n+1 (off-diagonal entries only)
+    std::vector<int32_t> col;       // new column indices
+    std::vector<double> T;          // -a_ij / a_ii
+    std::vector<double> d;          // a_ii (new order)
+    int64_t max_off = 0;            // longest off-diagonal row
+};
+
+// Row tiles (contiguous new-row ranges that never cross a partition) and
+// their assignment to CTAs.
+struct Tiling {
+    int32_t rows_per_tile = 256;
+    int32_t max_entries = 0;            // cap of off-diagonal entries in a staged tile
+    std::vector<int32_t> row0;          // ntiles+1 tile row boundaries
+    std::vector<int32_t> nnz0;          // ntiles+1: T-form rowptr at the boundaries
+    std::vector<int32_t> cta0;          // ctas+1 tile ranges per CTA
+    std::vector<int32_t> tile_part;     // partition of each tile
+    int64_t ntiles() const { return (int64_t)row0.size() - 1; }
+};
+
+struct Error {
+    jac_status st = JAC_OK;
+    std::string msg;
+    Error() = default;
+    Error(jac_status s, std::string m) : st(s), msg(std::move(m)) {}
+    bool ok() const { return st == JAC_OK; }
+};
+
+// jac_partition.cpp
+Error host_csr_from_abi(const jac_csr* A, bool transpose, HostCSR& out);   // A must be host memory
+Error make_plan(const HostCSR& A, jac_splitting s, int32_t nparts, const jac_opts& o, Plan& plan);
+Error make_tform(const HostCSR& A, const Plan& plan, TForm& tf);
+void dependency_lists(const HostCSR& A, const Plan& plan, std::vector<int64_t>& recv_ptr,
+                      std::vector<int32_t>& recv_from, std::vector<int64_t>& recv);
+void make_tiling(const TForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
+                 int64_t ctas, Tiling& t);
+HostCSR transpose_csr(const HostCSR& A);
+
+}  // namespace jac

@@ -1,0 +1,33 @@
+// Host-callable launchers of the kernels in jac_kernels.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "jac_device.cuh"
+
+namespace jac {
+
+cudaError_t launch_row_sweep(int phase, const DevMat& m, const DevVec& v, JacCtl* ctl, cudaStream_t s);
+
+// Persistent kernel instance for (rows per tile, pipeline stages, mixed cycle);
+// nullptr if that combination is not compiled.
+const void* persistent_kernel(int rows, int stages, bool mixed);
+int persistent_smem_bytes(int rows, int emax, int stages);
+cudaError_t launch_persistent(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
+                              const DevTiles& t, JacCtl* ctl, int max_sweeps, cudaStream_t s);
+
+cudaError_t launch_gather_rows(const long long* perm, const double* src, double* dst, int n, int nrhs,
+                               cudaStream_t s);
+cudaError_t launch_scatter_rows(const long long* perm, const double* src, double* dst, int n, int nrhs,
+                                cudaStream_t s);
+cudaError_t launch_make_c(const long long* perm, const double* b, const double* d, double* c, int n,
+                          JacCtl* ctl, cudaStream_t s);
+cudaError_t launch_arm(JacCtl* ctl, int test, int mixed, int inner, long long k_limit, long long k_delta,
+                       double tol, int norm_kind, double* hist, long long hist_cap, long long timeout, int skip,
+                       cudaStream_t s);
+cudaError_t launch_reset_iterate(JacCtl* ctl, cudaStream_t s);
+cudaError_t launch_reset_bar(JacCtl* ctl, cudaStream_t s);
+cudaError_t launch_adjoint_grad(const int* rowptr, const int* col, const double* lam, const double* x,
+                                double* dA, int n, cudaStream_t s);
+
+}  // namespace jac

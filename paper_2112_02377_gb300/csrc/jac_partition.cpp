@@ -1,0 +1,291 @@
+// Host-side splitting, reordering, dependency lists and tiling.
+//
+// Paper: band-row splitting (Sec. 4.2), the sparsity-pattern splitting with
+// receive/send dependency lists and nnz-weighted balancing (Sec. 4.2.2), and
+// substructuring with subdomain interiors first and the interface block last
+// (Sec. 4.3, block form Eq. (4.4)).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "jac_internal.h"
+
+namespace jac {
+
+static std::string fmt(const char* f, long long a = 0, long long b = 0, long long c = 0)
+{
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), f, a, b, c);
+    return buf;
+}
+
+Error host_csr_from_abi(const jac_csr* A, bool transpose, HostCSR& out)
+{
+    if (!A) return Error(JAC_EINVAL, "A is NULL");
+    if (A->n < 1) return Error(JAC_EINVAL, "n must be >= 1 (empty system)");
+    if (A->n >= (int64_t)INT32_MAX) return Error(JAC_EINVAL, "n must be < 2^31-1");
+    if (A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX) return Error(JAC_EINVAL, "nnz must be in [0, 2^31-1)");
+    if (A->index_base != 0 && A->index_base != 1) return Error(JAC_EINVAL, "index_base must be 0 or 1");
+    if (A->nnz > 0 && (!A->col || !A->val)) return Error(JAC_EINVAL, "col/val are NULL");
+    if (!A->rowptr) return Error(JAC_EINVAL, "rowptr is NULL");
+    const int64_t n = A->n, base = A->index_base;
+    if (A->rowptr[0] != base) return Error(JAC_EINVAL, "rowptr[0] must equal index_base");
+    if ((int64_t)A->rowptr[n] - base != A->nnz) return Error(JAC_EINVAL, "rowptr[n] - index_base must equal nnz");
+    HostCSR M;
+    M.n = n;
+    M.rowptr.resize(n + 1);
+    for (int64_t i = 0; i <= n; ++i) {
+        int64_t v = (int64_t)A->rowptr[i] - base;
+        if (i > 0 && v < M.rowptr[i - 1]) return Error(JAC_EINVAL, fmt("rowptr decreases at row %lld", i));
+        M.rowptr[i] = (int32_t)v;
+    }
+    M.col.resize(A->nnz);
+    M.val.resize(A->nnz);
+    for (int64_t k = 0; k < A->nnz; ++k) {
+        int64_t c = (int64_t)A->col[k] - base;
+        if (c < 0 || c >= n) return Error(JAC_EINVAL, fmt("column index out of range at entry %lld", k));
+        if (!std::isfinite(A->val[k])) return Error(JAC_EINVAL, fmt("non-finite value at entry %lld", k));
+        M.col[k] = (int32_t)c;
+        M.val[k] = A->val[k];
+    }
+    out = transpose ? transpose_csr(M) : std::move(M);
+    return Error();
+}
+
+HostCSR transpose_csr(const HostCSR& A)
+{
+    // Counting sort by column; rows of A^T list their entries in ascending
+    // original row order (stable for repeated (i, j) pairs).
+    HostCSR T;
+    T.n = A.n;
+    const int64_t nnz = A.nnz();
+    T.rowptr.assign(A.n + 1, 0);
+    for (int64_t k = 0; k < nnz; ++k) T.rowptr[A.col[k] + 1]++;
+    for (int64_t i = 0; i < A.n; ++i) T.rowptr[i + 1] += T.rowptr[i];
+    std::vector<int32_t> fill(T.rowptr.begin(), T.rowptr.end() - 1);
+    T.col.resize(nnz);
+    T.val.resize(nnz);
+    for (int64_t i = 0; i < A.n; ++i)
+        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+            int32_t pos = fill[A.col[k]]++;
+            T.col[pos] = (int32_t)i;
+            T.val[pos] = A.val[k];
+        }
+    return T;
+}
+
+// Substructuring: node-plane cuts c_t = floor(t g / p), t = 1..p-1.
+// Returns the number of cuts strictly below `coord` and whether coord is a cut.
+static inline void axis_side(int64_t coord, int64_t g, int64_t p, int64_t& below, bool& on)
+{
+    below = 0;
+    on = false;
+    for (int64_t t = 1; t < p; ++t) {
+        int64_t c = (t * g) / p;
+        if (c < coord) ++below;
+        else if (c == coord) on = true;
+    }
+}
+
+Error make_plan(const HostCSR& A, jac_splitting s, int32_t nparts, const jac_opts& o, Plan& plan)
+{
+    const int64_t n = A.n;
+    plan = Plan();
+    plan.splitting = s;
+    plan.perm.resize(n);
+    plan.iperm.resize(n);
+    if (s == JAC_BANDROW || s == JAC_BANDROW_NNZ) {
+        if (nparts < 1 || nparts > n) return Error(JAC_EINVAL, fmt("nparts must be in [1, n=%lld]", n));
+        const int64_t P = nparts;
+        plan.part_ptr.resize(P + 1);
+        if (s == JAC_BANDROW) {
+            for (int64_t p = 0; p <= P; ++p) plan.part_ptr[p] = (p * n) / P;
+        } else {
+            // first row r with P * IA(r) >= k * nnz (IA non-decreasing -> lower bound)
+            const int64_t nnz = A.nnz();
+            for (int64_t k = 0; k <= P; ++k) {
+                const int64_t target = k * nnz;
+                int64_t lo = 0, hi = n;
+                while (lo < hi) {
+                    int64_t mid = lo + (hi - lo) / 2;
+                    if (P * (int64_t)A.rowptr[mid] >= target) hi = mid;
+                    else lo = mid + 1;
+                }
+                plan.part_ptr[k] = lo;
+            }
+            plan.part_ptr[0] = 0;
+            plan.part_ptr[P] = n;
+        }
+        std::iota(plan.perm.begin(), plan.perm.end(), 0);
+        std::iota(plan.iperm.begin(), plan.iperm.end(), 0);
+        return Error();
+    }
+    if (s != JAC_SUBSTRUCT) return Error(JAC_EINVAL, "unknown splitting");
+    const int64_t gx = o.grid[0], gy = o.grid[1], gz = o.grid[2];
+    const int64_t px = o.subdomains[0], py = o.subdomains[1], pz = o.subdomains[2];
+    if (gx < 1 || gy < 1 || gz < 1) return Error(JAC_EINVAL, "SUBSTRUCT needs opts.grid (gx, gy, gz) >= 1");
+    if (px < 1 || py < 1 || pz < 1 || px > gx || py > gy || pz > gz)
+        return Error(JAC_EINVAL, "SUBSTRUCT needs 1 <= opts.subdomains[d] <= grid[d]");
+    const int64_t G = gx * gy * gz;
+    if (!o.node_of_row && n != G) return Error(JAC_EINVAL, "n != gx*gy*gz and no node_of_row given");
+    if (o.node_of_row) {
+        std::vector<uint8_t> seen(G, 0);
+        for (int64_t r = 0; r < n; ++r) {
+            int64_t v = o.node_of_row[r];
+            if (v < 0 || v >= G) return Error(JAC_EINVAL, fmt("node_of_row[%lld] outside the grid", r));
+            if (seen[v]) return Error(JAC_EINVAL, fmt("node_of_row repeats node %lld", v));
+            seen[v] = 1;
+        }
+    }
+    const int64_t S = px * py * pz;
+    std::vector<int64_t> sid(n);
+    // precompute per-axis tables
+    std::vector<int64_t> bx(gx), by(gy), bz(gz);
+    std::vector<uint8_t> ox(gx), oy(gy), oz(gz);
+    for (int64_t v = 0; v < gx; ++v) { bool on; axis_side(v, gx, px, bx[v], on); ox[v] = on; }
+    for (int64_t v = 0; v < gy; ++v) { bool on; axis_side(v, gy, py, by[v], on); oy[v] = on; }
+    for (int64_t v = 0; v < gz; ++v) { bool on; axis_side(v, gz, pz, bz[v], on); oz[v] = on; }
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t node = o.node_of_row ? o.node_of_row[r] : r;
+        const int64_t X = node % gx, Y = (node / gx) % gy, Z = node / (gx * gy);
+        sid[r] = (ox[X] || oy[Y] || oz[Z]) ? S : bx[X] + px * (by[Y] + py * bz[Z]);
+    }
+    plan.part_ptr.assign(S + 2, 0);
+    for (int64_t r = 0; r < n; ++r) plan.part_ptr[sid[r] + 1]++;
+    for (int64_t p = 0; p <= S; ++p) plan.part_ptr[p + 1] += plan.part_ptr[p];
+    std::vector<int64_t> fill(plan.part_ptr.begin(), plan.part_ptr.end() - 1);
+    for (int64_t r = 0; r < n; ++r) {
+        int64_t pos = fill[sid[r]]++;
+        plan.perm[pos] = r;
+        plan.iperm[r] = pos;
+    }
+    plan.interface_rows = plan.part_ptr[S + 1] - plan.part_ptr[S];
+    // The block form of Eq. (4.4) needs A_ij = 0 between different interiors.
+    for (int64_t i = 0; i < n; ++i) {
+        if (sid[i] == S) continue;
+        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+            int64_t sj = sid[A.col[k]];
+            if (sj != S && sj != sid[i])
+                return Error(JAC_EINVAL, fmt("subdomain interiors %lld and %lld are coupled (row %lld): "
+                                             "grid/subdomains do not match the matrix", sid[i], sj, i));
+        }
+    }
+    return Error();
+}
+
+Error make_tform(const HostCSR& A, const Plan& plan, TForm& tf)
+{
+    const int64_t n = A.n;
+    tf = TForm();
+    tf.n = n;
+    tf.rowptr.resize(n + 1);
+    tf.d.resize(n);
+    tf.rowptr[0] = 0;
+    // pass 1: diagonal and off-diagonal counts
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t i = plan.perm[r];
+        int ndiag = 0;
+        double di = 0.0;
+        int64_t off = 0;
+        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+            if (A.col[k] == i) { ++ndiag; di = A.val[k]; }
+            else ++off;
+        }
+        if (ndiag > 1) return Error(JAC_EINVAL, fmt("row %lld stores its diagonal %lld times", i, ndiag));
+        if (ndiag == 0 || di == 0.0) return Error(JAC_ESINGULAR, fmt("zero or missing diagonal in row %lld", i));
+        tf.d[r] = di;
+        tf.rowptr[r + 1] = (int32_t)(tf.rowptr[r] + off);
+        tf.max_off = std::max(tf.max_off, off);
+    }
+    const int64_t nnz_off = tf.rowptr[n];
+    tf.col.resize(nnz_off);
+    tf.T.resize(nnz_off);
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t i = plan.perm[r];
+        const double di = tf.d[r];
+        int64_t w = tf.rowptr[r];
+        for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+            if (A.col[k] == i) continue;
+            tf.col[w] = (int32_t)plan.iperm[A.col[k]];
+            tf.T[w] = -(A.val[k] / di);
+            ++w;
+        }
+    }
+    return Error();
+}
+
+void dependency_lists(const HostCSR& A, const Plan& plan, std::vector<int64_t>& recv_ptr,
+                      std::vector<int32_t>& recv_from, std::vector<int64_t>& recv)
+{
+    const int64_t n = A.n, P = plan.nparts();
+    std::vector<int32_t> owner(n);
+    for (int64_t p = 0; p < P; ++p)
+        for (int64_t r = plan.part_ptr[p]; r < plan.part_ptr[p + 1]; ++r) owner[plan.perm[r]] = (int32_t)p;
+    std::vector<int64_t> stamp(n, -1);
+    recv_ptr.assign(P + 1, 0);
+    recv_from.clear();
+    recv.clear();
+    std::vector<std::pair<int32_t, int64_t>> ext;
+    for (int64_t p = 0; p < P; ++p) {
+        ext.clear();
+        for (int64_t r = plan.part_ptr[p]; r < plan.part_ptr[p + 1]; ++r) {
+            const int64_t i = plan.perm[r];
+            for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+                const int64_t j = A.col[k];
+                if (owner[j] != p && stamp[j] != p) {
+                    stamp[j] = p;
+                    ext.emplace_back(owner[j], j);
+                }
+            }
+        }
+        std::sort(ext.begin(), ext.end());
+        for (auto& e : ext) { recv_from.push_back(e.first); recv.push_back(e.second); }
+        recv_ptr[p + 1] = (int64_t)recv.size();
+    }
+}
+
+void make_tiling(const TForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
+                 int64_t ctas, Tiling& t)
+{
+    t = Tiling();
+    t.rows_per_tile = rows_per_tile;
+    t.max_entries = max_entries;
+    t.row0.push_back(0);
+    for (int64_t p = 0; p < plan.nparts(); ++p) {
+        int64_t r = plan.part_ptr[p];
+        const int64_t end = plan.part_ptr[p + 1];
+        while (r < end) {
+            int64_t rows = 0, ent = 0;
+            while (r + rows < end && rows < rows_per_tile) {
+                int64_t len = tf.rowptr[r + rows + 1] - tf.rowptr[r + rows];
+                if (rows > 0 && ent + len > max_entries) break;
+                ent += len;
+                ++rows;
+                if (ent > max_entries) break;   // a single oversized row forms its own tile
+            }
+            r += rows;
+            t.row0.push_back((int32_t)r);
+            t.tile_part.push_back((int32_t)p);
+        }
+    }
+    const int64_t nt = t.ntiles();
+    t.nnz0.resize(nt + 1);
+    for (int64_t i = 0; i <= nt; ++i) t.nnz0[i] = tf.rowptr[t.row0[i]];
+    // contiguous tile ranges per CTA, balanced by algorithmic bytes
+    std::vector<double> pre(nt + 1, 0.0);
+    for (int64_t i = 0; i < nt; ++i) {
+        double rows = t.row0[i + 1] - t.row0[i], ent = t.nnz0[i + 1] - t.nnz0[i];
+        pre[i + 1] = pre[i] + 12.0 * ent + 36.0 * rows;
+    }
+    t.cta0.assign(ctas + 1, 0);
+    int64_t cur = 0;
+    for (int64_t g = 1; g < ctas; ++g) {
+        const double target = pre[nt] * (double)g / (double)ctas;
+        while (cur < nt && pre[cur] + 0.5 * (pre[cur + 1] - pre[cur]) < target) ++cur;
+        t.cta0[g] = (int32_t)cur;
+    }
+    t.cta0[ctas] = (int32_t)nt;
+}
+
+}  // namespace jac

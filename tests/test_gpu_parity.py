@@ -1,0 +1,363 @@
+"""GPU parity: the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances (FP64 path).  One sweep computes x'_i = c_i + sum T_ij x_j with
+T_ij = -a_ij / a_ii, c_i = b_i / a_ii and fused multiply-adds; the oracle
+computes (1/a_ii)(b_i - sum a_ij x_j) with separately rounded operations.  Both
+are backward stable, so for the same input x the two results differ by at most
+a few units of roundoff times the row's magnitude
+    scale_i = (|b_i| + sum_{j != i} |a_ij x_j|) / |a_ii|,
+and we require |x_gpu - x_oracle|_i <= 1e-13 * scale_i (about 450 ulps of the
+row scale).  Residual norms: |relres_gpu - relres_oracle| <= 1e-13 *
+(||b|| + || |A| |x| ||) / ||b||.  Iterates of different splittings, tilings
+and kernel variants are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2112_02377_gb300 import jacobi as J
+from paper_2112_02377_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-13
+
+
+def _scale(A, b, x):
+    S = A.scipy()
+    d = S.diagonal()
+    absA = abs(S)
+    off = absA @ np.abs(x) - np.abs(d) * np.abs(x)
+    return (np.abs(b) + off) / np.abs(d)
+
+
+def _assert_sweep_close(A, b, x_in, x_gpu, x_ref):
+    sc = _scale(A, b, x_in)
+    err = np.abs(x_gpu - x_ref)
+    bad = err > RTOL * sc + 1e-300
+    assert not bad.any(), f"{bad.sum()} rows outside 1e-13*scale; worst ratio {np.max(err / (sc + 1e-300)):.3e}"
+
+
+def _relres_tol(A, b, x):
+    bn = np.linalg.norm(b)
+    return RTOL * (bn + np.linalg.norm(abs(A.scipy()) @ np.abs(x))) / (bn if bn > 0 else 1.0)
+
+
+def _setup(A, b, split, nparts=4, variant=0, sub=(2, 2, 2), **kw):
+    s = J.SPLITTINGS[split]
+    o = J.opts(variant=variant, **kw)
+    node = None
+    if s == J.JAC_SUBSTRUCT:
+        o.grid[:] = list(A.grid)
+        o.subdomains[:] = list(sub)
+        node = A.node
+    return J.jac_setup(A, b, s, nparts, o, node_of_row=node)
+
+
+SPLITS = [("bandrow", 4), ("bandrow_nnz", 5), ("substruct", 0)]
+
+
+def _cases():
+    A = W.laplace7(16)
+    yield "lap7_16", A, W.solution_and_rhs(A, 0)[1]
+    A = W.fe27_deleted(11, seed=2)
+    yield "fe27_11", A, W.solution_and_rhs(A, 5)[1]
+    A = W.diffusion7((13, 9, 10), seed=4)
+    yield "diff7_ragged", A, W.solution_and_rhs(A, 6)[1]
+    A = W.convection7(9, peclet=0.9)
+    yield "conv7", A, W.solution_and_rhs(A, 8)[1]
+
+
+@pytest.mark.parametrize("name,A,b", list(_cases()))
+@pytest.mark.parametrize("variant", [1, 2])
+def test_per_sweep_parity_and_splitting_invariance(name, A, b, variant):
+    rng = np.random.default_rng(1)
+    x0 = rng.uniform(-1, 1, A.n)
+    Mo = O.prepare(A)
+    finals = []
+    for split, P in SPLITS:
+        ctx = _setup(A, b, split, P, variant=variant)
+        try:
+            J.jac_set_x(ctx, x0)
+            x = x0.copy()
+            for k in range(6):
+                rel = J.jac_sweep(ctx, 1)
+                xg = J.jac_get_x(ctx)
+                y, ss, mx = O.sweep(Mo, b, x)
+                _assert_sweep_close(A, b, x, xg, y)
+                assert abs(rel - np.sqrt(ss) / np.linalg.norm(b)) <= _relres_tol(A, b, x)
+                x = xg
+            J.jac_sweep(ctx, 40)
+            finals.append(J.jac_get_x(ctx))
+            st = J.jac_stats(ctx)
+            assert st["k"] == 46
+        finally:
+            J.jac_free(ctx)
+    for f in finals[1:]:
+        assert np.array_equal(f, finals[0])
+
+
+@pytest.mark.parametrize("name,A,b", list(_cases())[:2])
+def test_variants_and_graph_batching_are_bit_identical(name, A, b):
+    outs = []
+    for variant, K, rows in [(1, 64, 256), (2, 64, 256), (2, 7, 256), (2, 1, 256), (2, 64, 512), (2, 5, 512)]:
+        ctx = _setup(A, b, "bandrow", 3, variant=variant, sweeps_per_graph=K, tile_rows=rows)
+        try:
+            J.jac_sweep(ctx, 23)
+            J.jac_sweep(ctx, 14)
+            outs.append(J.jac_get_x(ctx))
+        finally:
+            J.jac_free(ctx)
+    ctx = _setup(A, b, "bandrow", 3, variant=2)
+    try:
+        for _ in range(37):
+            J.jac_sweep(ctx, 1)
+        outs.append(J.jac_get_x(ctx))
+    finally:
+        J.jac_free(ctx)
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("split,P", SPLITS)
+def test_config1_solve_16cubed_to_1e6(variant, split, P):
+    """16^3 7-point Laplace, b = A x* (seed 0), x0 = 0, relative residual 1e-6:
+    the oracle (and the DST closed form) take 637 sweeps."""
+    A = W.laplace7(16)
+    xs, b = W.solution_and_rhs(A, 0)
+    xo, ko, relo, sto, hist_o = O.solve(A, b, tol=1e-6, maxit=5000, history=True)
+    assert ko == 637
+    ctx = _setup(A, b, split, P, variant=variant, history=4096)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-6, 5000)
+        assert st == J.JAC_OK and k == ko
+        assert abs(rel - relo) <= 1e-12
+        xg = J.jac_get_x(ctx)
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-12
+        h = J.jac_get_history(ctx)
+        assert len(h) == k + 1
+        assert np.max(np.abs(h - hist_o)) < 1e-12
+    finally:
+        J.jac_free(ctx)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_paper_q1_count_with_inf_norm(variant):
+    """The paper's cube-35937 run: 746 iterations to ||r||_inf < 1e-8 (Sec. 5.2)."""
+    A, b = W.q1_laplace(33)
+    ctx = _setup(A, b, "bandrow_nnz", 8, variant=variant, norm=J.JAC_NORM_INF)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-8, 10000)
+        assert st == J.JAC_OK and k + 1 == 746
+    finally:
+        J.jac_free(ctx)
+
+
+def test_maxit_returns_notconv_with_valid_iterate():
+    A = W.laplace7(12)
+    xs, b = W.solution_and_rhs(A, 2)
+    xo, ko, relo, sto = O.solve(A, b, tol=1e-12, maxit=50)
+    assert sto == O.JO_ENOTCONV and ko == 50
+    ctx = _setup(A, b, "bandrow", 2)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-12, 50)
+        assert st == J.JAC_ENOTCONV and k == 50
+        assert abs(rel - relo) < 1e-12
+        assert np.linalg.norm(J.jac_get_x(ctx) - xo) <= 1e-12 * np.linalg.norm(xo)
+    finally:
+        J.jac_free(ctx)
+
+
+# ------------------------------------------------------------ edge cases --
+
+def test_one_by_one_and_diagonal_systems():
+    A = W.dense_to_csr(np.array([[4.0]]))
+    ctx = _setup(A, np.array([2.0]), "bandrow", 1)
+    try:
+        k, rel, st = J.jac_solve(ctx, 0.0, 5)
+        assert st == J.JAC_OK and k == 1 and rel == 0.0
+        assert J.jac_get_x(ctx)[0] == 0.5
+    finally:
+        J.jac_free(ctx)
+    d = np.random.default_rng(3).uniform(1, 2, 700)
+    A = W.dense_to_csr(np.diag(d))
+    b = np.random.default_rng(4).uniform(-1, 1, 700)
+    for variant in (1, 2):
+        ctx = _setup(A, b, "bandrow", 7, variant=variant)
+        try:
+            k, rel, st = J.jac_solve(ctx, 0.0, 5)
+            assert st == J.JAC_OK and k == 1
+            np.testing.assert_allclose(J.jac_get_x(ctx), O.sweep(A, b, np.zeros(700))[0], rtol=2.3e-16, atol=0)
+        finally:
+            J.jac_free(ctx)
+
+
+def test_one_row_per_partition_and_zero_rhs():
+    A = W.random_dominant(50, seed=9, density=0.2)
+    b = np.random.default_rng(0).uniform(-1, 1, 50)
+    x_ref = O.solve(A, b, tol=1e-13, maxit=5000)[0]
+    ctx = _setup(A, b, "bandrow", 50)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-13, 5000)
+        assert st == J.JAC_OK
+        assert np.linalg.norm(J.jac_get_x(ctx) - x_ref) < 1e-12
+    finally:
+        J.jac_free(ctx)
+    ctx = _setup(A, None, "bandrow", 3)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-10, 100)
+        assert st == J.JAC_OK and k == 0 and rel == 0.0
+    finally:
+        J.jac_free(ctx)
+
+
+def test_device_memory_and_one_based_inputs():
+    import torch
+    A = W.fe27_deleted(8, seed=7)
+    xs, b = W.solution_and_rhs(A, 1)
+    ref = None
+    for mode in ("host0", "host1", "dev0"):
+        if mode == "host0":
+            ctx = J.jac_setup(A, b, J.JAC_BANDROW, 3, J.opts())
+        elif mode == "host1":
+            ctx = J.jac_setup((A.rowptr + 1, A.col + 1, A.val), b, J.JAC_BANDROW, 3, J.opts(), index_base=1)
+        else:
+            dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            ctx = J.jac_setup((dv(A.rowptr), dv(A.col), dv(A.val)), dv(b), J.JAC_BANDROW, 3, J.opts())
+        try:
+            J.jac_sweep(ctx, 30)
+            if mode == "dev0":
+                out = torch.empty(A.n, dtype=torch.float64, device="cuda")
+                J.jac_get_x(ctx, out)
+                x = out.cpu().numpy()
+            else:
+                x = J.jac_get_x(ctx)
+        finally:
+            J.jac_free(ctx)
+        if ref is None:
+            ref = x
+        assert np.array_equal(x, ref)
+
+
+def test_set_x_resume_equals_continuous_run():
+    A = W.laplace7(10)
+    xs, b = W.solution_and_rhs(A, 3)
+    ctx = _setup(A, b, "substruct", 0)
+    try:
+        J.jac_sweep(ctx, 30)
+        mid = J.jac_get_x(ctx)
+        J.jac_sweep(ctx, 20)
+        full = J.jac_get_x(ctx)
+        J.jac_set_x(ctx, mid)
+        J.jac_sweep(ctx, 20)
+        assert np.array_equal(J.jac_get_x(ctx), full)
+        assert J.jac_stats(ctx)["k"] == 20
+    finally:
+        J.jac_free(ctx)
+
+
+def test_errors_singular_duplicate_diagonal_divergence():
+    M = np.array([[1.0, 2.0], [3.0, 0.0]])
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup(W.dense_to_csr(M), np.ones(2), J.JAC_BANDROW, 1)
+    assert ei.value.status == J.JAC_ESINGULAR
+    A = W.dense_to_csr(np.array([[2.0, 1.0], [1.0, 2.0]]))
+    B = W.CSR(2, np.array([0, 3, 5], np.int32), np.array([0, 0, 1, 0, 1], np.int32),
+              np.array([1.0, 1.0, 1.0, 1.0, 2.0]))
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup(B, np.ones(2), J.JAC_BANDROW, 1)
+    assert ei.value.status == J.JAC_EINVAL
+    # rho(T) >> 1: the iterate overflows and the residual becomes Inf/NaN
+    D = np.array([[1e-200, 1.0, 0.0], [1.0, 1e-200, 1.0], [0.0, 1.0, 1e-200]])
+    for variant in (1, 2):
+        ctx = J.jac_setup(W.dense_to_csr(D), np.ones(3), J.JAC_BANDROW, 1, J.opts(variant=variant))
+        try:
+            with pytest.raises(J.JacobiError) as ei:
+                J.jac_solve(ctx, 1e-8, 100)
+            assert ei.value.status == J.JAC_ENUMERIC
+        finally:
+            J.jac_free(ctx)
+
+
+def test_grid_barrier_timeout_is_reported_and_recoverable():
+    """One CTA never arrives at the grid barrier (host-set hook); the others
+    give up after a short bounded wait and the call reports JAC_ETIMEOUT."""
+    A = W.laplace7(24)
+    xs, b = W.solution_and_rhs(A, 0)
+    ctx = J.jac_setup(A, b, J.JAC_BANDROW, 4, J.opts(variant=2, fault_skip_cta=1, timeout_cycles=20_000_000))
+    try:
+        with pytest.raises(J.JacobiError) as ei:
+            J.jac_sweep(ctx, 5)
+        assert ei.value.status == J.JAC_ETIMEOUT
+    finally:
+        J.jac_free(ctx)
+    ctx = _setup(A, b, "bandrow", 4, variant=2)
+    try:
+        J.jac_sweep(ctx, 5)
+        x = J.jac_get_x(ctx)
+        y = np.zeros(A.n)
+        for _ in range(5):
+            y = O.sweep(A, b, y)[0]
+        assert np.linalg.norm(x - y) <= 1e-13 * np.linalg.norm(y)
+    finally:
+        J.jac_free(ctx)
+
+
+# ---------------------------------------------------- mixed precision ----
+
+@pytest.mark.parametrize("variant,rows", [(1, 256), (2, 256), (2, 512)])
+def test_mixed_precision_reaches_1e10(variant, rows):
+    A = W.laplace7(16)
+    xs, b = W.solution_and_rhs(A, 0)
+    x64, k64, rel64, st64 = O.solve(A, b, tol=1e-10, maxit=20000)
+    ctx = _setup(A, b, "bandrow", 4, variant=variant, precision=J.JAC_MIXED, inner_sweeps=64, tile_rows=rows)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-10, 20000)
+        assert st == J.JAC_OK
+        x = J.jac_get_x(ctx)
+        r = b - O.spmv(A, x)
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+        assert abs(rel - np.linalg.norm(r) / np.linalg.norm(b)) < 1e-13
+        assert k > 0 and k % 64 == 0 and k64 - 64 <= k <= k64 + 3 * 64
+        assert np.linalg.norm(x - x64) / np.linalg.norm(x64) < 1e-8
+    finally:
+        J.jac_free(ctx)
+
+
+# ------------------------------------------------- full size (160^3) -----
+
+@pytest.fixture(scope="module")
+def big():
+    A = W.laplace7(160)
+    xs, b = W.solution_and_rhs(A, 0)
+    return A, b
+
+
+def test_full_size_160cubed_per_sweep_parity_all_splittings(big):
+    """The benchmark's workload and launch configuration: every element of
+    three consecutive sweeps against the oracle fed the same input, for each
+    splitting; then 61 more sweeps and the three iterates compared bit for bit."""
+    A, b = big
+    rng = np.random.default_rng(11)
+    x0 = rng.uniform(-1, 1, A.n)
+    Mo = O.prepare(A)
+    finals = []
+    for split, P in [("bandrow", 64), ("bandrow_nnz", 64), ("substruct", 0)]:
+        ctx = _setup(A, b, split, P, variant=2, sub=(4, 4, 4))
+        try:
+            J.jac_set_x(ctx, x0)
+            x = x0
+            for k in range(3):
+                rel = J.jac_sweep(ctx, 1)
+                xg = J.jac_get_x(ctx)
+                y, ss, mx = O.sweep(Mo, b, x)
+                _assert_sweep_close(A, b, x, xg, y)
+                assert abs(rel - np.sqrt(ss) / np.linalg.norm(b)) <= _relres_tol(A, b, x)
+                x = xg
+            J.jac_sweep(ctx, 61)
+            finals.append(J.jac_get_x(ctx))
+        finally:
+            J.jac_free(ctx)
+    for f in finals[1:]:
+        assert np.array_equal(f, finals[0])

@@ -1,0 +1,168 @@
+"""CPU tests of the C ABI: the library loads, exports every declared symbol,
+and its host-side splitting / dependency-list logic equals the oracle's
+(bit-exact integer work).  No GPU work is launched here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT, golden_path
+from oracle import oracle as O
+from paper_2112_02377_gb300 import jacobi as J
+from paper_2112_02377_gb300 import workloads as W
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "jacobi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(jac_[a-z_]+)\s*\(", src)))
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    L = J.lib()
+    declared = _header_functions()
+    assert len(declared) >= 16
+    for name in declared:
+        assert hasattr(L, name), name
+    assert sorted(J.EXPORTED) == declared
+
+
+def _matrices():
+    yield "lap7_12", W.laplace7(12), None
+    yield "lap7_box", W.laplace7((9, 7, 11)), None
+    yield "diff7", W.diffusion7((10, 8, 6), seed=3), None
+    F = W.fe27_deleted(9, seed=1)
+    yield "fe27", F, F.node
+
+
+@pytest.mark.parametrize("name,A,node", list(_matrices()))
+def test_band_splittings_match_oracle(name, A, node):
+    for P in (1, 2, 3, 7, 64):
+        perm, parts = J.jac_partition_plan(A, J.JAC_BANDROW, P)
+        assert np.array_equal(perm, np.arange(A.n))
+        assert np.array_equal(parts, O.band_row_parts(A.n, P))
+        perm, parts = J.jac_partition_plan(A, J.JAC_BANDROW_NNZ, P)
+        assert np.array_equal(parts, O.band_nnz_parts(A.rowptr, P))
+
+
+@pytest.mark.parametrize("name,A,node", list(_matrices()))
+def test_substructuring_matches_oracle(name, A, node):
+    for sub in [(1, 1, 1), (2, 2, 2), (3, 2, 1), (2, 1, 3)]:
+        o = J.opts(grid=A.grid, subdomains=sub)
+        perm, parts = J.jac_partition_plan(A, J.JAC_SUBSTRUCT, 0, o, node_of_row=node)
+        p2, pp2 = O.substructure(A.grid, sub, A.n, node=node)
+        assert np.array_equal(perm, p2)
+        assert np.array_equal(parts, pp2)
+
+
+def test_substructuring_160_cube_interface_size():
+    A = W.laplace7(40)
+    o = J.opts(grid=(40, 40, 40), subdomains=(4, 4, 4))
+    perm, parts = J.jac_partition_plan(A, J.JAC_SUBSTRUCT, 0, o)
+    assert len(parts) == 66
+    assert parts[-1] - parts[-2] == 40 ** 3 - 37 ** 3
+
+
+@pytest.mark.parametrize("name,A,node", list(_matrices()))
+def test_dependency_lists_match_oracle(name, A, node):
+    for s, P in [(J.JAC_BANDROW, 4), (J.JAC_BANDROW_NNZ, 5)]:
+        rptr, rfrom, recv = J.jac_dependency_lists(A, s, P)
+        parts = O.band_row_parts(A.n, P) if s == J.JAC_BANDROW else O.band_nnz_parts(A.rowptr, P)
+        rcv, _ = O.dependency_lists(A.rowptr, A.col, parts)
+        hp, h = O.halo_of(rcv)
+        assert np.array_equal(rptr[: P + 1], hp)
+        assert np.array_equal(recv, h)
+        owner = O.owner_of_rows(parts, np.arange(A.n), A.n)
+        assert np.array_equal(rfrom, owner[recv])
+    o = J.opts(grid=A.grid, subdomains=(2, 2, 2))
+    rptr, rfrom, recv = J.jac_dependency_lists(A, J.JAC_SUBSTRUCT, 0, o, node_of_row=node)
+    perm, parts = O.substructure(A.grid, (2, 2, 2), A.n, node=node)
+    rcv, _ = O.dependency_lists(A.rowptr, A.col, parts, perm)
+    hp, h = O.halo_of(rcv)
+    assert np.array_equal(rptr[: len(hp)], hp)
+    assert np.array_equal(recv, h)
+    # interiors receive only from the interface (Eq. (4.4) block structure)
+    S = len(parts) - 2
+    for p in range(S):
+        assert np.all(rfrom[rptr[p]:rptr[p + 1]] == S)
+
+
+def test_dependency_lists_reproduce_paper_example():
+    pat = W.paper_pattern_10x10()
+    A = W.dense_to_csr(pat.astype(float) + 10 * np.eye(10))
+    rptr, rfrom, recv = J.jac_dependency_lists(A, J.JAC_BANDROW, 3)
+    got = {}
+    for p in range(3):
+        for q, j in zip(rfrom[rptr[p]:rptr[p + 1]], recv[rptr[p]:rptr[p + 1]]):
+            got.setdefault((p + 1, int(q) + 1), []).append(int(j) + 1)
+    want = {}
+    for line in open(golden_path("dependency_10x10_3bands.txt")):
+        line = line.split("#")[0].strip()
+        if line.startswith("recv"):
+            head, nodes = line.split(":")
+            _, a, _, b = head.split()
+            want[(int(a), int(b))] = [int(v) for v in nodes.split()]
+    assert got == want
+
+
+def test_one_based_input_is_accepted():
+    A = W.laplace7(6)
+    A1 = W.CSR(A.n, A.rowptr + 1, A.col + 1, A.val)
+    csr, keep = J.make_csr(A1.rowptr, A1.col, A1.val, A.n, index_base=1)
+    import ctypes
+    perm = np.empty(A.n, dtype=np.int64)
+    part = np.empty(4, dtype=np.int64)
+    cnt = ctypes.c_int64()
+    st = J.lib().jac_partition_plan(ctypes.byref(csr), J.JAC_BANDROW_NNZ, 3, ctypes.byref(J.opts()),
+                                    ctypes.c_void_p(perm.ctypes.data), ctypes.c_void_p(part.ctypes.data),
+                                    ctypes.byref(cnt))
+    assert st == J.JAC_OK
+    assert np.array_equal(part, O.band_nnz_parts(A.rowptr, 3))
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    ("col_range", "column index out of range"),
+    ("rowptr_dec", "rowptr decreases"),
+    ("nparts0", "nparts"),
+    ("nparts_big", "nparts"),
+    ("sub_nogrid", "grid"),
+    ("sub_coupled", "coupled"),
+    ("sub_toomany", "subdomains"),
+    ("nonfinite", "non-finite"),
+])
+def test_invalid_inputs_are_rejected(mutate, msg):
+    A = W.laplace7(6)
+    rp, col, val = A.rowptr.copy(), A.col.copy(), A.val.copy()
+    s, P, o = J.JAC_BANDROW, 3, J.opts()
+    if mutate == "col_range":
+        col[5] = A.n
+    elif mutate == "rowptr_dec":
+        rp[10] = rp[12]
+    elif mutate == "nparts0":
+        P = 0
+    elif mutate == "nparts_big":
+        P = A.n + 1
+    elif mutate == "sub_nogrid":
+        s = J.JAC_SUBSTRUCT
+    elif mutate == "sub_coupled":
+        s, o = J.JAC_SUBSTRUCT, J.opts(grid=(3, 12, 6), subdomains=(2, 2, 2))
+    elif mutate == "sub_toomany":
+        s, o = J.JAC_SUBSTRUCT, J.opts(grid=(6, 6, 6), subdomains=(7, 1, 1))
+    elif mutate == "nonfinite":
+        val[3] = np.nan
+    B = W.CSR(A.n, rp, col, val)
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_partition_plan(B, s, P, o)
+    assert ei.value.status == J.JAC_EINVAL
+    assert msg in str(ei.value)
+
+
+def test_setup_without_a_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    A = W.laplace7(4)
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup(A, np.ones(A.n), J.JAC_BANDROW, 2)
+    assert ei.value.status == J.JAC_ECUDA
