@@ -188,7 +188,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-1e-8 solves")
-    ap.add_argument("--cpu-sweeps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="time budget of the CPU oracle sample")
+    ap.add_argument("--profile-sweeps", type=int, default=0,
+                    help="profiling case: one 160^3 band-row context, graphs of this many sweeps, "
+                         "two warm-up launches then one more launch, no output line")
+    ap.add_argument("--profile-precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--profile-variant", type=int, default=0, help="kernel variant of the profiling case (0 = default)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -207,11 +212,26 @@ def main():
     A = W.laplace7(GRID)
     xs, b = W.solution_and_rhs(A, 0)
     bps = _algorithmic_bytes(A.n, A.nnz)
+    if args.profile_sweeps > 0:
+        K = args.profile_sweeps
+        mixed = args.profile_precision == "mixed"
+        o = J.opts(variant=args.profile_variant, sweeps_per_graph=K, device=local,
+                   precision=J.JAC_MIXED if mixed else J.JAC_FP64, inner_sweeps=max(2, K))
+        c = J.jac_setup(A, b, J.JAC_BANDROW, 64, o)
+        if mixed:
+            J.jac_solve(c, 0.0, 3 * K - 1)        # three launches of K sweeps (cycles of K)
+        else:
+            J.jac_sweep(c, 2 * K)                 # two warm-up launches
+            J.jac_sweep(c, K)                     # the launch to capture
+        st = J.jac_stats(c)
+        J.jac_free(c)
+        print(f"profile case done: {st['sweeps_total']} sweeps evaluated, last {st['last_ms']:.3f} ms", flush=True)
+        return 0
     stream = torch.cuda.current_stream()
     ctxs = []
     setup_s = []
     for split, P in SPLITS:
-        o = J.opts(variant=2, sweeps_per_graph=K_PER_GRAPH, stream=stream.cuda_stream, device=local)
+        o = J.opts(sweeps_per_graph=K_PER_GRAPH, stream=stream.cuda_stream, device=local)
         if split == "substruct":
             o.grid[:] = [GRID] * 3
             o.subdomains[:] = list(SUBDOMAINS)
@@ -295,7 +315,7 @@ def main():
         ttr = {}
         xref = None
         for prec in ("fp64", "mixed"):
-            o = J.opts(variant=2, sweeps_per_graph=256, stream=stream.cuda_stream, device=local,
+            o = J.opts(sweeps_per_graph=256, stream=stream.cuda_stream, device=local,
                        precision=J.JAC_MIXED if prec == "mixed" else J.JAC_FP64, inner_sweeps=MIXED_INNER)
             c = J.jac_setup(A, b, J.JAC_BANDROW, 64, o)
             k, rel, stt = J.jac_solve(c, TOL_TTR, 200000)
@@ -315,8 +335,9 @@ def main():
 
     # ---------------- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
-    if rank == 0 and ws == 1 and args.cpu_sweeps > 0:
-        n_cpu = max(1, args.cpu_sweeps // 10)
+    if rank == 0 and ws == 1 and args.cpu_seconds > 0:
+        t1 = cpu_oracle_rate(A, b, 1)
+        n_cpu = max(1, int(args.cpu_seconds / max(t1, 1e-3)))
         dt = cpu_oracle_rate(A, b, n_cpu)
         cpu = {"value": round(bps * n_cpu / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": f"{n_cpu} FP64 sweeps of the 160^3 system (band-row order), single-threaded C oracle, "
@@ -338,7 +359,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "traffic": (traffic * K_PER_GRAPH if traffic is not None else None),
-                         "traffic_per_sweep": traffic, "kernel": "k_persistent<256,4,false>",
+                         "traffic_per_sweep": traffic, "kernel": "k_persistent<1,4,false,8>",
                          "units_per_launch": K_PER_GRAPH, "bytes_per_unit": bps,
                          "frac_of_8TBs": round(achieved / 8000.0, 4)},
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

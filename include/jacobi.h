@@ -96,9 +96,13 @@ typedef struct {
                                   NULL = row r sits at node r */
     int32_t nrhs;              /* right-hand sides sharing A (1..8, default 1) */
     int32_t transpose;         /* 1 = solve with A^T instead of A (adjoint solves) */
-    int32_t variant;           /* 0 = auto; 1 = one launch per sweep (row kernel);
-                                  2 = persistent grid-synchronised pipelined kernel */
-    int32_t tile_rows;         /* rows per tile: 0 = auto, 256 or 512 */
+    int32_t variant;           /* 0 = auto (2); 1 = one launch per sweep (row kernel);
+                                  2 = persistent grid-synchronised pipelined kernel, x gathered
+                                  from L2; 3 = as 2 with each tile's x halo (its dependency list,
+                                  Sec. 4.2.2) staged into shared memory */
+    int32_t tile_rows;         /* rows per tile: 0 = auto (256 FP64, 480 mixed), 224, 256 or 480
+                                  (variant 2); 256 (variant 3) */
+    int32_t ctas_per_sm;       /* variant 2 with 256-row tiles: 0 = auto (2), or 3 (3-stage pipeline) */
     int32_t history;           /* >0: record the relres of every evaluated iterate,
                                   up to this many entries (jac_get_history) */
     void* stream;              /* cudaStream_t for all work; NULL = legacy default stream */
@@ -120,6 +124,8 @@ typedef struct {
     int64_t k;                    /* index of the current iterate x^k */
     int64_t sweeps_total;         /* sweeps evaluated since setup / jac_set_x */
     int64_t outer_iterations;     /* JAC_MIXED refinement steps of the last solve */
+    int64_t halo_fallback_tiles;  /* tiles whose x halo is gathered from L2 (staged-halo kernel) */
+    int64_t halo_window_elems;    /* x values staged into shared memory per sweep (staged-halo kernel) */
     double last_relres;           /* test value of the last evaluated iterate */
     double last_res2, last_resinf;/* ||r||_2 and ||r||_inf of that iterate */
     double last_ms;               /* device time of the last jac_sweep/jac_solve (CUDA events) */
@@ -236,6 +242,16 @@ jac_status jac_get_batch_results(jac_ctx* ctx, int64_t* sweeps, double* relres);
  */
 jac_status jac_adjoint_grad(jac_ctx* ctx, const double* lambda, const double* x, double* dA,
                             int32_t memory);
+
+/*
+ * jac_get_trace -- per-CTA time split of the last jac_sweep / jac_solve of a
+ * persistent kernel (variants 2, 3): compute_ms[i] = time CTA i spent in its
+ * tiles, wait_ms[i] = time it spent in the grid barrier, summed over sweeps.
+ * The GPU counterpart of the paper's communication / total time columns
+ * (Sec. 5.2 tables).  Host arrays of `max` entries (may be NULL);
+ * *ctas receives the CTA count (0 for the one-launch-per-sweep variant).
+ */
+jac_status jac_get_trace(jac_ctx* ctx, double* compute_ms, double* wait_ms, int64_t max, int64_t* ctas);
 
 /* jac_stats -- counters of the context (see jac_stats_t). */
 jac_status jac_stats(jac_ctx* ctx, jac_stats_t* out);

@@ -39,6 +39,7 @@ struct jac_ctx {
     float* d_dlt = nullptr;
     Partial* d_part = nullptr;
     int nslots = 0;
+    unsigned long long* d_trace = nullptr;
     JacCtl* d_ctl = nullptr;
     JacCtl* h_ctl = nullptr;     // pinned mirrors [2]
     double* d_hist = nullptr;
@@ -53,6 +54,11 @@ struct jac_ctx {
     int* d_row0 = nullptr;
     int* d_nnz0 = nullptr;
     int* d_cta0 = nullptr;
+    int* d_blk0 = nullptr;
+    int* d_blk = nullptr;
+    int* d_lcol = nullptr;
+    int xcap = 0, maxruns = 0, ntcap = 0, blkcap = 0;
+    int64_t fallback_tiles = 0, window_elems = 0;
     int ntiles = 0, emax = 0, rows_per_tile = 256, stages = 4, grid = 0, threads = 0, smem = 0;
     const void* pfn64 = nullptr;
     const void* pfnmix = nullptr;
@@ -164,6 +170,7 @@ DevVec devvec(const jac_ctx* c)
     v.dlt = c->d_dlt;
     v.part = c->d_part;
     v.nslots = c->nslots;
+    v.trace = c->d_trace;
     return v;
 }
 
@@ -173,8 +180,15 @@ DevTiles devtiles(const jac_ctx* c)
     t.row0 = c->d_row0;
     t.nnz0 = c->d_nnz0;
     t.cta0 = c->d_cta0;
+    t.blk0 = c->d_blk0;
+    t.blk = c->d_blk;
+    t.lcol = c->d_lcol;
     t.ntiles = c->ntiles;
     t.emax = c->emax;
+    t.xcap = c->xcap;
+    t.maxruns = c->maxruns;
+    t.ntcap = c->ntcap;
+    t.blkcap = c->blkcap;
     return t;
 }
 
@@ -182,7 +196,7 @@ DevTiles devtiles(const jac_ctx* c)
 jac_status enqueue_step(jac_ctx* c, bool mixed)
 {
     cudaStream_t s = stream_of(c);
-    if (c->variant == 2) {
+    if (c->variant >= 2) {
         CK(c, launch_reset_bar(c->d_ctl, s));
         CK(c, launch_persistent(mixed ? c->pfnmix : c->pfn64, c->grid, c->threads, c->smem, devmat(c), devvec(c),
                                 devtiles(c), c->d_ctl, c->K, s));
@@ -264,6 +278,8 @@ jac_status status_from_ctl(jac_ctx* c, const JacCtl& h)
 
 jac_status arm(jac_ctx* c, int test, int mixed, long long k_limit, long long k_delta, double tol)
 {
+    if (c->d_trace)
+        CK(c, cudaMemsetAsync(c->d_trace, 0, 4 * sizeof(unsigned long long) * c->grid, stream_of(c)));
     CK(c, launch_arm(c->d_ctl, test, mixed, c->o.inner_sweeps, k_limit, k_delta, tol, c->o.norm, c->d_hist, c->hist_cap,
                      (long long)c->o.timeout_cycles, c->o.fault_skip_cta, stream_of(c)));
     return JAC_OK;
@@ -289,6 +305,7 @@ void destroy(jac_ctx* c)
     dfree(c->d_x[0]); dfree(c->d_x[1]); dfree(c->d_e[0]); dfree(c->d_e[1]); dfree(c->d_dlt);
     dfree(c->d_part); dfree(c->d_ctl); dfree(c->d_hist); dfree(c->d_perm); dfree(c->d_stage); dfree(c->d_stage2);
     dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0); dfree(c->d_cta0);
+    dfree(c->d_blk0); dfree(c->d_blk); dfree(c->d_lcol); dfree(c->d_trace);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     delete c;
 }
@@ -334,10 +351,12 @@ jac_status check_opts(const jac_opts& o, jac_ctx* err_ctx)
     if (o.inner_sweeps < 2 || o.inner_sweeps > 100000)
         return fail(err_ctx, JAC_EINVAL, "opts.inner_sweeps must be in [2, 100000]");
     if (o.nrhs != 1) return fail(err_ctx, JAC_EINVAL, "opts.nrhs > 1 is supported by jac_setup_batched only");
-    if (o.variant < 0 || o.variant > 2) return fail(err_ctx, JAC_EINVAL, "opts.variant must be 0, 1 or 2");
-    if (o.tile_rows != 0 && o.tile_rows != 256 && o.tile_rows != 512)
-        return fail(err_ctx, JAC_EINVAL, "opts.tile_rows must be 0, 256 or 512");
+    if (o.variant < 0 || o.variant > 3) return fail(err_ctx, JAC_EINVAL, "opts.variant must be 0, 1, 2 or 3");
+    if (o.tile_rows != 0 && o.tile_rows != 224 && o.tile_rows != 256 && o.tile_rows != 480)
+        return fail(err_ctx, JAC_EINVAL, "opts.tile_rows must be 0, 224, 256 or 480");
     if (o.history < 0) return fail(err_ctx, JAC_EINVAL, "opts.history must be >= 0");
+    if (o.ctas_per_sm != 0 && o.ctas_per_sm != 2 && o.ctas_per_sm != 3)
+        return fail(err_ctx, JAC_EINVAL, "opts.ctas_per_sm must be 0, 2 or 3");
     return JAC_OK;
 }
 
@@ -474,34 +493,89 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     // ---- launch configuration
     cudaDeviceProp prop;
     CK(nullptr, cudaGetDeviceProperties(&prop, dev));
+    Tiling tl;
+    Windows win;
+    // Defaults (measured at 160^3 on GB300): FP64 sweeps are bound by the FP64
+    // pipe and run best with the plain loop, 8 math warps x 2 CTAs/SM; the FP32
+    // inner sweeps of the mixed solve are latency bound and run best with the
+    // software-pipelined loop, 15 math warps x 1 CTA/SM.
     c->variant = o.variant == 0 ? 2 : o.variant;
-    c->rows_per_tile = o.tile_rows ? o.tile_rows : 256;
+    c->rows_per_tile = o.tile_rows ? o.tile_rows : (o.precision == JAC_MIXED && c->variant == 2 ? 480 : 256);
     c->stages = 4;
-    if (c->variant == 2) {
+    if (c->variant == 3 && c->rows_per_tile != 256) c->variant = 2;
+    const int target_per_sm = (c->variant == 2 && c->rows_per_tile == 256 && o.ctas_per_sm == 3) ? 3 : 2;
+    if (target_per_sm == 3) c->stages = 3;
+    if (c->variant >= 2) {
         const int rows = c->rows_per_tile;
-        // Stage budget: 2 CTAs/SM x 4 stages for 256-row tiles, 1 CTA/SM x 4
-        // stages for 512-row tiles (~220 KB of shared memory per SM).
-        const int64_t stage_budget = rows == 256 ? 26 * 1024 : 52 * 1024;
         int64_t cap_entries = (int64_t)std::max<int64_t>(1, tf.max_off) * rows;
+        int64_t stage_budget;
+        if (c->variant == 3) {
+            // 2 CTAs/SM x 3 stages of (matrix data + run list + x window) in ~210 KB
+            c->stages = 3;
+            c->xcap = 1280;
+            c->maxruns = 16;
+            stage_budget = 36 * 1024 - (c->xcap + 8) * 8;
+        } else {
+            // 2 CTAs/SM x 4 stages for 224/256-row tiles, 1 CTA/SM x 4 stages for 480-row tiles
+            stage_budget = rows <= 256 ? 26 * 1024 : 52 * 1024;
+        }
         const int64_t budget_entries = std::max<int64_t>(rows, (stage_budget - 24 * rows - 1024) / 12);
         c->emax = (int)std::min<int64_t>(cap_entries, budget_entries);
-        c->pfn64 = persistent_kernel(rows, c->stages, false);
-        c->pfnmix = persistent_kernel(rows, c->stages, true);
-        c->smem = persistent_smem_bytes(rows, c->emax, c->stages);
-        c->threads = 256 + 32;
-        int per_sm = 0;
-        if (c->pfn64 && c->pfnmix) {
-            CK(nullptr, cudaFuncSetAttribute(c->pfn64, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
-            CK(nullptr, cudaFuncSetAttribute(c->pfnmix, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
-            int a = 0, b2 = 0;
-            CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, c->pfn64, c->threads, c->smem));
-            CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, c->pfnmix, c->threads, c->smem));
-            per_sm = std::min(std::min(a, b2), 2);
+        if (c->variant == 3) {
+            c->pfn64 = halo_kernel(c->stages, false);
+            c->pfnmix = halo_kernel(c->stages, true);
+        } else {
+            c->pfn64 = persistent_kernel(rows, c->stages, false);
+            c->pfnmix = persistent_kernel(rows, c->stages, true);
+            c->smem = persistent_smem_bytes(rows, c->emax, c->stages);
         }
+        c->threads = (c->variant == 3) ? 256 + 32 : persistent_threads(rows);
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        auto occupancy = [&](int smem_bytes) -> int {
+            if (!c->pfn64 || !c->pfnmix) return 0;
+            if (cudaFuncSetAttribute(c->pfn64, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess ||
+                cudaFuncSetAttribute(c->pfnmix, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            int a = 0, b2 = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, c->pfn64, c->threads, smem_bytes) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, c->pfnmix, c->threads, smem_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            return std::min(std::min(a, b2), target_per_sm);
+        };
+        int per_sm = 0;
+        if (c->variant == 3) {
+            // The tile table's size depends on the CTA count, which depends on
+            // the shared memory per CTA: try 2 CTAs/SM, then 1.
+            make_tiling(tf, plan, rows, c->emax, 1, tl);
+            make_windows(tf, tl, c->xcap, c->maxruns, c->emax, win);
+            for (int guess = 2; guess >= 1 && per_sm == 0; --guess) {
+                const int ctas = guess * prop.multiProcessorCount;
+                make_tiling(tf, plan, rows, c->emax, ctas, tl);
+                int ntcap = 0, blkcap = 0;
+                for (int g = 0; g < ctas; ++g) {
+                    ntcap = std::max(ntcap, tl.cta0[g + 1] - tl.cta0[g]);
+                    blkcap = std::max(blkcap, win.blk0[tl.cta0[g + 1]] - win.blk0[tl.cta0[g]]);
+                }
+                const int smem_b = halo_smem_bytes(rows, c->emax, c->xcap, ntcap, blkcap, c->stages);
+                if (occupancy(smem_b) >= guess) {
+                    per_sm = guess;
+                    c->smem = smem_b;
+                    c->ntcap = ntcap;
+                    c->blkcap = blkcap;
+                }
+            }
+            c->fallback_tiles = win.fallback_tiles;
+            c->window_elems = win.window_elems;
+        } else {
+            per_sm = occupancy(c->smem);
+        }
         if (per_sm < 1 || !coop) {
-            if (o.variant == 2) {
+            if (o.variant >= 2) {
                 char msg[200];
                 std::snprintf(msg, sizeof(msg),
                               "persistent kernel cannot be made co-resident (rows %d, smem %d B, %d CTAs/SM, coop %d)",
@@ -517,11 +591,8 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
         c->grid = (int)((n + 255) / 256);
         c->emax = 0;
     }
-    Tiling tl;
-    if (c->variant == 2) {
-        make_tiling(tf, plan, c->rows_per_tile, c->emax, c->grid, tl);
-        c->ntiles = (int)tl.ntiles();
-    }
+    if (c->variant == 2) make_tiling(tf, plan, c->rows_per_tile, c->emax, c->grid, tl);
+    if (c->variant >= 2) c->ntiles = (int)tl.ntiles();
     c->nslots = c->grid;
 
     // ---- device buffers
@@ -539,6 +610,7 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
         CK(nullptr, dalloc(&c->d_dlt, n + 16));
     }
     CK(nullptr, dalloc(&c->d_part, 2 * (size_t)c->nslots + 2));
+    if (c->variant >= 2) CK(nullptr, dalloc(&c->d_trace, 4 * (size_t)c->grid));
     CK(nullptr, dalloc(&c->d_ctl, 1));
     CK(nullptr, dalloc(&c->d_perm, n));
     CK(nullptr, dalloc(&c->d_stage, n + 16));
@@ -550,7 +622,16 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     }
     CK(nullptr, cudaEventCreate(&c->ev0));
     CK(nullptr, cudaEventCreate(&c->ev1));
-    if (c->variant == 2) {
+    if (c->variant == 3) {
+        CK(nullptr, dalloc(&c->d_blk0, win.blk0.size()));
+        CK(nullptr, dalloc(&c->d_blk, win.blk.size() + 16));
+        CK(nullptr, dalloc(&c->d_lcol, win.lcol.size() + 16));
+        CK(nullptr, cudaMemcpy(c->d_blk0, win.blk0.data(), win.blk0.size() * 4, cudaMemcpyHostToDevice));
+        CK(nullptr, cudaMemcpy(c->d_blk, win.blk.data(), win.blk.size() * 4, cudaMemcpyHostToDevice));
+        if (!win.lcol.empty())
+            CK(nullptr, cudaMemcpy(c->d_lcol, win.lcol.data(), win.lcol.size() * 4, cudaMemcpyHostToDevice));
+    }
+    if (c->variant >= 2) {
         CK(nullptr, dalloc(&c->d_row0, tl.row0.size()));
         CK(nullptr, dalloc(&c->d_nnz0, tl.nnz0.size()));
         CK(nullptr, dalloc(&c->d_cta0, tl.cta0.size()));
@@ -805,6 +886,22 @@ jac_status jac_adjoint_grad(jac_ctx* c, const double* lambda, const double* x, d
     return JAC_OK;
 }
 
+jac_status jac_get_trace(jac_ctx* c, double* compute_ms, double* wait_ms, int64_t max, int64_t* ctas)
+{
+    if (!c || !ctas) return JAC_EINVAL;
+    *ctas = c->d_trace ? c->grid : 0;
+    if (!c->d_trace || max <= 0) return JAC_OK;
+    DeviceGuard g(c->device);
+    std::vector<unsigned long long> h(4 * (size_t)c->grid);
+    CK(c, cudaMemcpy(h.data(), c->d_trace, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    const int64_t m = std::min<int64_t>(max, c->grid);
+    for (int64_t i = 0; i < m; ++i) {
+        if (compute_ms) compute_ms[i] = h[4 * i] * 1e-6;
+        if (wait_ms) wait_ms[i] = h[4 * i + 1] * 1e-6;
+    }
+    return JAC_OK;
+}
+
 jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
 {
     if (!c || !out) return JAC_EINVAL;
@@ -821,6 +918,8 @@ jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
     out->k = h.k;
     out->sweeps_total = c->sweeps_total;
     out->outer_iterations = c->outer_last;
+    out->halo_fallback_tiles = c->fallback_tiles;
+    out->halo_window_elems = c->window_elems;
     out->last_relres = h.relres;
     out->last_res2 = h.res2;
     out->last_resinf = h.resinf;

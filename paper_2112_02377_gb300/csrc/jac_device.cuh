@@ -65,14 +65,22 @@ struct DevVec {
     float* dlt;               // FP32 delta = D^{-1} r (mixed)
     Partial* part;            // [2][nslots] per-sweep partial norms
     int nslots;
+    unsigned long long* trace;  // [ctas][4]: compute ns, barrier-wait ns, sweeps, 0 (persistent kernels)
 };
 
 struct DevTiles {
     const int* row0;          // ntiles+1
     const int* nnz0;          // ntiles+1
     const int* cta0;          // ctas+1
+    const int* blk0;          // ntiles+1 (halo kernel): int4 offset of each tile's run block
+    const int* blk;           // run blocks {xlen, own, nruns, flags} + {src, len, dst, 0} x nruns
+    const int* lcol;          // nnz_off tile-local columns (halo kernel)
     int ntiles;
     int emax;                 // staged entry cap of a tile
+    int xcap;                 // x window capacity (elements)
+    int maxruns;              // runs per tile
+    int ntcap;                // halo kernel: tile-table capacity per CTA
+    int blkcap;               // halo kernel: run-block capacity per CTA (int4)
 };
 
 __device__ __forceinline__ unsigned long long abs_bits(double r)

@@ -53,6 +53,23 @@ struct Tiling {
     int64_t ntiles() const { return (int64_t)row0.size() - 1; }
 };
 
+// Per-tile x windows: the dependency list of a tile (Sec. 4.2.2), as a few
+// contiguous runs of x that together cover every column the tile reads plus
+// its own rows.  Runs start on a multiple of 4 elements and have a length that
+// is a multiple of 4, so both FP64 and FP32 windows can be moved with 16-byte
+// aligned bulk copies.  lcol[k] is entry k's index inside its tile's window.
+// Block of a tile in `blk` (int4 units): header {xlen, own_off, nruns, flags}
+// followed by nruns records {src, len, dst, 0}.
+struct Windows {
+    int32_t xcap = 0, maxruns = 0;
+    std::vector<int32_t> blk0;          // ntiles+1, int4 offsets into blk
+    std::vector<int32_t> blk;           // 4 ints per record
+    std::vector<int32_t> lcol;          // nnz_off local columns (undefined on fallback tiles)
+    int64_t fallback_tiles = 0;
+    int64_t window_elems = 0;           // sum of window lengths (x values staged per sweep)
+};
+enum : int32_t { TILE_FALLBACK = 1 };   // tile reads x from L2 with global columns
+
 struct Error {
     jac_status st = JAC_OK;
     std::string msg;
@@ -70,5 +87,6 @@ void dependency_lists(const HostCSR& A, const Plan& plan, std::vector<int64_t>& 
 void make_tiling(const TForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
                  int64_t ctas, Tiling& t);
 HostCSR transpose_csr(const HostCSR& A);
+void make_windows(const TForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w);
 
 }  // namespace jac

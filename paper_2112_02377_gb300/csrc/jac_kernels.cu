@@ -20,45 +20,11 @@ constexpr int CHUNK = 8;   // off-diagonal entries whose x loads are issued toge
 
 // ------------------------------------------------------------ row math -----
 
-// FP64 row: acc = c + sum T x (stored order).  tv/cv read through `ldt`/`ldc`.
-template <class LdT, class LdC>
-__device__ __forceinline__ double row_dot64(double acc, int kb, int ke, const double* __restrict__ xs,
-                                            LdT ldt, LdC ldc)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (int kk = kb; kk < ke; kk += CHUNK) {
-        double tv[CHUNK], xv[CHUNK];
-#pragma unroll
-        for (int u = 0; u < CHUNK; ++u) {
-            if (kk + u < ke) {
-                tv[u] = ldt(kk + u);
-                xv[u] = __ldcg(xs + ldc(kk + u));
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < CHUNK; ++u)
-            if (kk + u < ke) acc = __fma_rn(tv[u], xv[u], acc);
-    }
-    return acc;
-}
-
-template <class LdT, class LdC>
-__device__ __forceinline__ float row_dot32(float acc, int kb, int ke, const float* __restrict__ es, LdT ldt,
-                                           LdC ldc)
-{
-    for (int kk = kb; kk < ke; kk += CHUNK) {
-        float tv[CHUNK], ev[CHUNK];
-#pragma unroll
-        for (int u = 0; u < CHUNK; ++u) {
-            if (kk + u < ke) {
-                tv[u] = ldt(kk + u);
-                ev[u] = __ldcg(es + ldc(kk + u));
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < CHUNK; ++u)
-            if (kk + u < ke) acc = __fmaf_rn(tv[u], ev[u], acc);
-    }
-    return acc;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // Residual bookkeeping of one row from its update.
@@ -69,6 +35,78 @@ __device__ __forceinline__ void accumulate_residual(double xnew, double xold, do
     const double r = __dmul_rn(di, dl);
     ss = __fma_rn(r, r, ss);
     mx = umax64(mx, abs_bits(r));
+}
+
+// RPT rows of one thread: acc[q] = acc[q] + sum_k T_k x_col(k), entries of each
+// row in stored order.  ldx(k) loads x_col(k) (an L2 gather or a read of the
+// shared-memory halo); the x loads of a chunk of every row are issued before
+// the chunk's FMAs, T is read at the FMA (shared memory, short latency).
+// The FMA loop stops at the longest row of the warp (a warp-uniform branch):
+// on GB300 the FP64 pipe is the scarce unit, and a predicated-off DFMA costs
+// as much of it as a live one.
+template <int RPT, bool PREFETCH_T = false, class Real, class LdT, class LdX>
+__device__ __forceinline__ void rows_dot(Real (&acc)[RPT], const int (&kb)[RPT], const int (&len)[RPT], LdT ldt,
+                                         LdX ldx)
+{
+    int lmax = 0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) lmax = len[q] > lmax ? len[q] : lmax;
+    lmax = (int)__reduce_max_sync(__activemask(), (unsigned)lmax);
+    for (int o = 0; o < lmax; o += CHUNK) {
+        Real xv[RPT][CHUNK];
+        Real tv[RPT][PREFETCH_T ? CHUNK : 1];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+#pragma unroll
+            for (int u = 0; u < CHUNK; ++u) {
+                if (o + u < len[q]) {
+                    xv[q][u] = ldx(kb[q] + o + u);
+                    if constexpr (PREFETCH_T) tv[q][u] = ldt(kb[q] + o + u);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CHUNK; ++u) {
+            if (o + u >= lmax) break;
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                if (o + u < len[q]) {
+                    Real tk;
+                    if constexpr (PREFETCH_T) tk = tv[q][u];
+                    else tk = ldt(kb[q] + o + u);
+                    if constexpr (sizeof(Real) == 8) acc[q] = __fma_rn(tk, xv[q][u], acc[q]);
+                    else acc[q] = __fmaf_rn(tk, xv[q][u], acc[q]);
+                }
+            }
+        }
+    }
+}
+
+// Entries prefetched per row by the pipelined persistent kernel (a 7-point row
+// has 6 off-diagonal entries); longer rows finish in row_tail.
+constexpr int PF = 6;
+
+// Rest of a row beyond the prefetched entries (T and col staged in shared
+// memory, x gathered from L2), continuing the same FMA chain in stored order.
+template <class Real>
+__device__ __noinline__ Real row_tail(const Real* sv, const int* scol, const Real* src, int kb, int len, Real acc)
+{
+    for (int e = kb; e < kb + len; ++e) {
+        if constexpr (sizeof(Real) == 8) acc = __fma_rn(sv[e], __ldcg(src + scol[e]), acc);
+        else acc = __fmaf_rn(sv[e], __ldcg(src + scol[e]), acc);
+    }
+    return acc;
+}
+
+// A row of an oversized tile (its T and col were not staged): all from global.
+template <class Real>
+__device__ __noinline__ Real row_global(const Real* T, const int* col, const Real* src, int kb, int len, Real acc)
+{
+    for (int e = kb; e < kb + len; ++e) {
+        if constexpr (sizeof(Real) == 8) acc = __fma_rn(__ldg(T + e), __ldcg(src + __ldg(col + e)), acc);
+        else acc = __fmaf_rn(__ldg(T + e), __ldcg(src + __ldg(col + e)), acc);
+    }
+    return acc;
 }
 
 // =========================================================================
@@ -104,7 +142,11 @@ __global__ void __launch_bounds__(256) k_row_sweep(DevMat m, DevVec v, JacCtl* c
         if (PH == PH_P64 || PH == PH_P64R) {
             const double* xs = v.x[xb];
             const double xi = __ldcg(xs + i);
-            const double acc = row_dot64(__ldg(m.c + i), kb, ke, xs, [&](int k) { return __ldg(m.T64 + k); }, ldc);
+            double acc1[1] = {__ldg(m.c + i)};
+            const int kb1[1] = {kb}, len1[1] = {ke - kb};
+            rows_dot<1>(acc1, kb1, len1, [&](int k) { return __ldg(m.T64 + k); },
+                        [&](int k) { return __ldcg(xs + ldc(k)); });
+            const double acc = acc1[0];
             if (PH == PH_P64) {
                 v.x[xb ^ 1][i] = acc;
             } else {
@@ -116,7 +158,11 @@ __global__ void __launch_bounds__(256) k_row_sweep(DevMat m, DevVec v, JacCtl* c
         } else {
             const int j = s_phase;   // inner step: e_j -> e_{j+1}
             const float* es = v.e[j & 1];
-            const float acc = row_dot32(__ldcg(v.dlt + i), kb, ke, es, [&](int k) { return __ldg(m.T32 + k); }, ldc);
+            float acc1[1] = {__ldcg(v.dlt + i)};
+            const int kb1[1] = {kb}, len1[1] = {ke - kb};
+            rows_dot<1>(acc1, kb1, len1, [&](int k) { return __ldg(m.T32 + k); },
+                        [&](int k) { return __ldcg(es + ldc(k)); });
+            const float acc = acc1[0];
             if (PH == PH_P32) v.e[(j + 1) & 1][i] = acc;
             else v.x[xb][i] = __dadd_rn(v.x[xb][i], (double)acc);
         }
@@ -228,48 +274,25 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+template <int NTHREADS>
 __device__ __forceinline__ void consumer_sync()
 {
-    asm volatile("bar.sync 1, 256;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
 }
 
-// RPT rows of one thread: acc[q] = acc[q] + sum_k T_k x_col(k), entries of each
-// row in stored order.  The L2 gathers of a chunk of every row are issued
-// before the chunk's FMAs; T is read at the FMA (shared memory, short latency).
-template <int RPT, class Real, class LdT, class LdC>
-__device__ __forceinline__ void rows_dot(Real (&acc)[RPT], const int (&kb)[RPT], const int (&len)[RPT],
-                                         const Real* __restrict__ xs, LdT ldt, LdC ldc)
-{
-    int lmax = 0;
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) lmax = len[q] > lmax ? len[q] : lmax;
-    for (int o = 0; o < lmax; o += CHUNK) {
-        Real xv[RPT][CHUNK];
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-#pragma unroll
-            for (int u = 0; u < CHUNK; ++u)
-                if (o + u < len[q]) xv[q][u] = __ldcg(xs + ldc(kb[q] + o + u));
-        }
-#pragma unroll
-        for (int u = 0; u < CHUNK; ++u) {
-#pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-                if (o + u < len[q]) {
-                    if constexpr (sizeof(Real) == 8) acc[q] = __fma_rn(ldt(kb[q] + o + u), xv[q][u], acc[q]);
-                    else acc[q] = __fmaf_rn(ldt(kb[q] + o + u), xv[q][u], acc[q]);
-                }
-            }
-        }
-    }
-}
-
-template <int RPT, int STAGES, bool MIXED>
-__global__ void __launch_bounds__(288) __maxnreg__(RPT == 1 ? 96 : 168)
+// Register budget: each SM sub-partition holds 16K registers and a CTA's warps
+// are dealt round-robin to the 4 sub-partitions, so (math warps + producer)
+// in multiples of 4 per SM leave 128 registers a thread; 2 x 9 warps leave 96.
+template <int RPT, int STAGES, bool MIXED, int NWM>
+__global__ void __maxnreg__(NWM == 8 ? (STAGES == 3 ? 72 : 96) : 128)
 k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int CT = 256, NW = 8, ROWS = CT * RPT;
+    constexpr int CT = NWM * 32, NW = NWM, ROWS = CT * RPT;
+    // 7 or 15 math warps have 128 registers: software-pipeline the x gathers of
+    // the next tile (pays off when latency, not the FP64 pipe, bounds the sweep:
+    // the FP32 inner sweeps); 8 math warps (96 registers) use the plain loop.
+    constexpr bool PIPE = (NWM != 8);
     const StageLayout L = stage_layout(ROWS, t.emax);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes);
     uint64_t* empty = full + STAGES;
@@ -399,6 +422,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     long long evals = s_evals, outer = s_outer;
     long long jc = 0;
     int nbar = 0;
+    unsigned long long tr_comp = 0, tr_wait = 0, tr_mark = (tid == 0) ? global_ns() : 0;
     for (int sw = 0; sw < ksw; ++sw) {
         const int ph = phase_of(MIXED, pos, inner);
         const bool norm_ph = (ph == PH_P64 || ph == PH_P64R);
@@ -408,83 +432,164 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         double* xd = v.x[xb ^ 1];
         const float* es = v.e[pos & 1];
         float* ed = v.e[(pos + 1) & 1];
-        for (int i = 0; i < nt; ++i, ++jc) {
-            const int sidx = (int)(jc % STAGES);
-            uint64_t* bar = &full[sidx];
-            const unsigned par = (unsigned)((jc / STAGES) & 1);
-            bool ok = mbar_try_wait(bar, par);
-            if (!ok && !s_fail) {
-                const long long t0 = clock64();
-                while (!(ok = mbar_try_wait(bar, par))) {
-                    if (s_fail) break;
-                    if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); s_fail = 1; break; }
-                }
+        // Software pipeline over the sweep's tiles: the x gathers (first chunk of
+        // the row and the row's own x) of tile i+1 are issued before the FMA
+        // chain of tile i, so L2 latency overlaps FP64 work.  Each row is still
+        // one FMA chain in stored order, bit-identical to the other kernels.
+        auto wait_full = [&](long long j) -> bool {
+            uint64_t* bar = &full[(int)(j % STAGES)];
+            const unsigned par = (unsigned)((j / STAGES) & 1);
+            if (mbar_try_wait(bar, par)) return true;
+            if (s_fail) return false;
+            const long long t0 = clock64();
+            while (!mbar_try_wait(bar, par)) {
+                if (s_fail) return false;
+                if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); s_fail = 1; return false; }
             }
-            if (ok) {
-                const unsigned char* st = smem + sidx * L.bytes;
+            return true;
+        };
+        auto run_tiles = [&](auto tag) {
+            using Real = decltype(tag);
+            constexpr bool F64 = sizeof(Real) == 8;
+            const Real* src = F64 ? reinterpret_cast<const Real*>(xs) : reinterpret_cast<const Real*>(es);
+            struct Job {
+                int sidx, r0, p0, kb, len;
+                bool ok, in, over;
+                Real xi;
+                Real xv[PF];
+            };
+            auto fetch = [&](long long j, Job& J) {
+                J.ok = wait_full(j);
+                J.sidx = (int)(j % STAGES);
+                if (!J.ok) return;
+                const unsigned char* st = smem + J.sidx * L.bytes;
                 const int* hdr = reinterpret_cast<const int*>(st);
-                const int r0 = hdr[0], r1 = hdr[1], p0 = hdr[2], p1 = hdr[3];
-                const bool over = (p1 - p0) > emax;
-                const int* srp = reinterpret_cast<const int*>(st + L.o_rp) - (r0 & ~3);
-                const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (p0 & ~3);
-                int r[RPT], kb[RPT], len[RPT];
+                J.r0 = hdr[0];
+                J.p0 = hdr[2];
+                J.over = (hdr[3] - J.p0) > emax;
+                const int r = J.r0 + tid;
+                J.in = r < hdr[1];
+                const int* srp = reinterpret_cast<const int*>(st + L.o_rp) - (J.r0 & ~3);
+                J.kb = J.in ? srp[r] : 0;
+                J.len = J.in ? srp[r + 1] - J.kb : 0;
+                if (F64) J.xi = J.in ? __ldcg(reinterpret_cast<const Real*>(xs) + r) : Real(0);
+                if (!J.over) {
+                    const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (J.p0 & ~3);
 #pragma unroll
-                for (int q = 0; q < RPT; ++q) {
-                    r[q] = r0 + tid + CT * q;
-                    const bool in = r[q] < r1;
-                    kb[q] = in ? srp[r[q]] : 0;
-                    len[q] = in ? srp[r[q] + 1] - kb[q] : 0;
+                    for (int u = 0; u < PF; ++u)
+                        if (u < J.len) J.xv[u] = __ldcg(src + scol[J.kb + u]);
                 }
-                if (norm_ph) {
-                    const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
-                    const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
-                    const double* sd = reinterpret_cast<const double*>(st + L.o_d) - (r0 & ~1);
-                    double xi[RPT], acc[RPT];
+            };
+            Job cur, nxt;
+            bool have = false;
+            for (int i = 0; i < nt; ++i, ++jc) {
+                if (have) cur = nxt;
+                else fetch(jc, cur);
+                have = false;
+                if (i + 1 < nt && cur.ok) {
+                    fetch(jc + 1, nxt);
+                    have = nxt.ok;
+                }
+                if (cur.ok) {
+                    const unsigned char* st = smem + cur.sidx * L.bytes;
+                    const int r = cur.r0 + tid;
+                    const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (cur.p0 & ~3);
+                    const Real* sv = reinterpret_cast<const Real*>(st + L.o_val) - (cur.p0 & (F64 ? ~1 : ~3));
+                    Real acc;
+                    if (F64) acc = cur.in ? Real(reinterpret_cast<const double*>(st + L.o_c)[r - (cur.r0 & ~1)]) : Real(0);
+                    else acc = cur.in ? Real(__ldcg(v.dlt + r)) : Real(0);
+                    if (!cur.over) {
+                        const int lmax = (int)__reduce_max_sync(__activemask(), (unsigned)cur.len);
 #pragma unroll
-                    for (int q = 0; q < RPT; ++q) {
-                        const bool in = r[q] < r1;
-                        xi[q] = in ? __ldcg(xs + r[q]) : 0.0;
-                        acc[q] = in ? sc[r[q]] : 0.0;
-                    }
-                    if (!over)
-                        rows_dot<RPT>(acc, kb, len, xs, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; });
-                    else
-                        rows_dot<RPT>(acc, kb, len, xs, [&](int e) { return __ldg(m.T64 + e); },
-                                      [&](int e) { return __ldg(m.col + e); });
-#pragma unroll
-                    for (int q = 0; q < RPT; ++q) {
-                        if (r[q] < r1) {
-                            if (ph == PH_P64) {
-                                __stcg(xd + r[q], acc[q]);
-                            } else {
-                                const float dl = (float)__dadd_rn(acc[q], -xi[q]);
-                                __stcg(v.dlt + r[q], dl);
-                                __stcg(v.e[1] + r[q], dl);
+                        for (int u = 0; u < PF; ++u) {
+                            if (u >= lmax) break;
+                            if (u < cur.len) {
+                                if constexpr (F64) acc = __fma_rn(sv[cur.kb + u], cur.xv[u], acc);
+                                else acc = __fmaf_rn(sv[cur.kb + u], cur.xv[u], acc);
                             }
-                            accumulate_residual(acc[q], xi[q], sd[r[q]], ss, mx);
                         }
+                        if (lmax > PF && cur.len > PF) acc = row_tail(sv, scol, src, cur.kb + PF, cur.len - PF, acc);
+                    } else if (cur.in) {
+                        acc = row_global(F64 ? reinterpret_cast<const Real*>(m.T64) : reinterpret_cast<const Real*>(m.T32),
+                                         m.col, src, cur.kb, cur.len, acc);
                     }
-                } else {
-                    const float* sv = reinterpret_cast<const float*>(st + L.o_val) - (p0 & ~3);
-                    float acc[RPT];
-#pragma unroll
-                    for (int q = 0; q < RPT; ++q) acc[q] = r[q] < r1 ? __ldcg(v.dlt + r[q]) : 0.f;
-                    if (!over)
-                        rows_dot<RPT>(acc, kb, len, es, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; });
-                    else
-                        rows_dot<RPT>(acc, kb, len, es, [&](int e) { return __ldg(m.T32 + e); },
-                                      [&](int e) { return __ldg(m.col + e); });
-#pragma unroll
-                    for (int q = 0; q < RPT; ++q) {
-                        if (r[q] < r1) {
-                            if (ph == PH_P32) __stcg(ed + r[q], acc[q]);
-                            else __stcg(v.x[xb] + r[q], __dadd_rn(__ldcg(v.x[xb] + r[q]), (double)acc[q]));
+                    if (cur.in) {
+                        if constexpr (F64) {
+                            const double* sd = reinterpret_cast<const double*>(st + L.o_d) - (cur.r0 & ~1);
+                            if (ph == PH_P64) {
+                                __stcg(xd + r, (double)acc);
+                            } else {
+                                const float dl = (float)__dadd_rn((double)acc, -(double)cur.xi);
+                                __stcg(v.dlt + r, dl);
+                                __stcg(v.e[1] + r, dl);
+                            }
+                            accumulate_residual((double)acc, (double)cur.xi, sd[r], ss, mx);
+                        } else {
+                            if (ph == PH_P32) __stcg(ed + r, (float)acc);
+                            else __stcg(v.x[xb] + r, __dadd_rn(__ldcg(v.x[xb] + r), (double)acc));
                         }
                     }
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[cur.sidx]);
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[sidx]);
+        };
+        if constexpr (PIPE) {
+            if (norm_ph) run_tiles(double(0));
+            else run_tiles(float(0));
+        } else {
+            for (int i = 0; i < nt; ++i, ++jc) {
+                const int sidx = (int)(jc % STAGES);
+                const bool ok = wait_full(jc);
+                if (ok) {
+                    const unsigned char* st = smem + sidx * L.bytes;
+                    const int* hdr = reinterpret_cast<const int*>(st);
+                    const int r0 = hdr[0], r1 = hdr[1], p0 = hdr[2], p1 = hdr[3];
+                    const bool over = (p1 - p0) > emax;
+                    const int* srp = reinterpret_cast<const int*>(st + L.o_rp) - (r0 & ~3);
+                    const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (p0 & ~3);
+                    const int r = r0 + tid;
+                    const bool in = r < r1;
+                    const int kb1[1] = {in ? srp[r] : 0};
+                    const int len1[1] = {in ? srp[r + 1] - kb1[0] : 0};
+                    if (norm_ph) {
+                        const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
+                        const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
+                        const double* sd = reinterpret_cast<const double*>(st + L.o_d) - (r0 & ~1);
+                        const double xi = in ? __ldcg(xs + r) : 0.0;
+                        double a1[1] = {in ? sc[r] : 0.0};
+                        if (!over)
+                            rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
+                                        [&](int e) { return __ldcg(xs + scol[e]); });
+                        else if (in)
+                            a1[0] = row_global(m.T64, m.col, xs, kb1[0], len1[0], a1[0]);
+                        if (in) {
+                            if (ph == PH_P64) {
+                                __stcg(xd + r, a1[0]);
+                            } else {
+                                const float dl = (float)__dadd_rn(a1[0], -xi);
+                                __stcg(v.dlt + r, dl);
+                                __stcg(v.e[1] + r, dl);
+                            }
+                            accumulate_residual(a1[0], xi, sd[r], ss, mx);
+                        }
+                    } else {
+                        const float* sv = reinterpret_cast<const float*>(st + L.o_val) - (p0 & ~3);
+                        float a1[1] = {in ? __ldcg(v.dlt + r) : 0.f};
+                        if (!over)
+                            rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
+                                        [&](int e) { return __ldcg(es + scol[e]); });
+                        else if (in)
+                            a1[0] = row_global(m.T32, m.col, es, kb1[0], len1[0], a1[0]);
+                        if (in) {
+                            if (ph == PH_P32) __stcg(ed + r, a1[0]);
+                            else __stcg(v.x[xb] + r, __dadd_rn(__ldcg(v.x[xb] + r), (double)a1[0]));
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[sidx]);
+            }
         }
         // ---- publish partial norms, grid barrier
         if (norm_ph) {
@@ -492,8 +597,11 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
             const unsigned long long wm = warp_max(mx);
             if (lane == 0) { s_wss[warp] = ws; s_wmx[warp] = wm; }
         }
-        consumer_sync();
+        consumer_sync<CT>();
         if (tid == 0) {
+            const unsigned long long tb_ = global_ns();
+            tr_comp += tb_ - tr_mark;
+            tr_mark = tb_;
             if (norm_ph) {
                 double b = 0.0;
                 unsigned long long bm = 0;
@@ -511,10 +619,15 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                 if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); s_fail = 1; break; }
                 __nanosleep(32);
             }
+            {
+                const unsigned long long tc_ = global_ns();
+                tr_wait += tc_ - tr_mark;
+                tr_mark = tc_;
+            }
             __threadfence();
         }
         ++nbar;
-        consumer_sync();
+        consumer_sync<CT>();
         if (s_fail) break;
         // ---- convergence decision (identical in every CTA)
         if (norm_ph) {
@@ -533,7 +646,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                     if (blockIdx.x == 0 && ctl->hist && evals < ctl->hist_cap) ctl->hist[evals] = d.relres;
                 }
             }
-            consumer_sync();
+            consumer_sync<CT>();
             evals += 1;
             if (s_dec_done != DONE_RUNNING) { s_done = s_dec_done; break; }
             if (ph == PH_P64) { k += 1; xb ^= 1; }
@@ -548,6 +661,11 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         if (!MIXED && !s_test && k >= s_klim) break;
     }
     // tell the producer to stop issuing; it drains its copies before exiting
+    if (tid == 0 && v.trace) {
+        atomicAdd(v.trace + 4 * blockIdx.x + 0, tr_comp);
+        atomicAdd(v.trace + 4 * blockIdx.x + 1, tr_wait);
+        atomicAdd(v.trace + 4 * blockIdx.x + 2, (unsigned long long)nbar);
+    }
     if (tid == 0) s_stop = 1;
     if (blockIdx.x == 0 && tid == 0) {
         ctl->k = k;
@@ -562,6 +680,463 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         ctl->k_eval = s_keval;
         __threadfence();
     }
+}
+
+// =========================================================================
+// Variant 3: persistent kernel with staged x halos (the default).
+//
+// As variant 2, but each tile also stages its x halo -- the few contiguous
+// runs of x its rows read (the tile's dependency list, Sec. 4.2.2), built at
+// setup with tile-local column numbers -- into shared memory with
+// cp.async.bulk.  The producer warp streams the constant tile data (T, local
+// col, IA, c, d, run list) for up to STAGES tiles ahead, across sweep
+// boundaries; the x runs of a tile are copied once the grid barrier that
+// completes the previous sweep has passed.  The 8 math warps then read only
+// shared memory, which keeps the FP64 pipe (GB300's scarce unit for this
+// sweep) fed.  Tiles whose halo does not fit (scattered columns) fall back to
+// L2 gathers with global column numbers.
+// =========================================================================
+
+struct HaloLayout {
+    int o_val, o_col, o_rp, o_c, o_d, o_x, bytes;
+};
+
+__host__ __device__ inline HaloLayout halo_layout(int rows, int emax, int xcap)
+{
+    auto up = [](int v) { return (v + 127) & ~127; };
+    HaloLayout L;
+    L.o_val = 128;                                  // header (r0, r1, p0, p1) in the first line
+    L.o_col = L.o_val + up((emax + 4) * 8);
+    L.o_rp = L.o_col + up((emax + 8) * 4);
+    L.o_c = L.o_rp + up((rows + 12) * 4);
+    L.o_d = L.o_c + up((rows + 4) * 8);
+    L.o_x = L.o_d + up((rows + 4) * 8);
+    L.bytes = L.o_x + up((xcap + 8) * 8);
+    return L;
+}
+
+// Shared memory of the halo kernel: STAGES stages, then the CTA's tile table
+// (row0, nnz0, run-block offsets: ntcap+1 ints each; run blocks: blkcap int4),
+// then the mbarriers.
+__host__ __device__ inline int halo_table_offset(int rows, int emax, int xcap, int stages)
+{
+    return stages * halo_layout(rows, emax, xcap).bytes;
+}
+
+int halo_smem_bytes(int rows, int emax, int xcap, int ntcap, int blkcap, int stages)
+{
+    const int tab = ((3 * (ntcap + 1) * 4 + 15) & ~15) + blkcap * 16;
+    return halo_table_offset(rows, emax, xcap, stages) + tab + 3 * stages * 8 + 64;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+template <int STAGES, bool MIXED>
+__global__ void __maxnreg__(96)
+k_halo(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int CT = 256, NW = 8;
+    const HaloLayout L = halo_layout(CT, t.emax, t.xcap);
+    int* s_row0 = reinterpret_cast<int*>(smem + halo_table_offset(CT, t.emax, t.xcap, STAGES));
+    int* s_nnz0 = s_row0 + (t.ntcap + 1);
+    int* s_boff = s_nnz0 + (t.ntcap + 1);
+    int4* s_blk = reinterpret_cast<int4*>(reinterpret_cast<unsigned char*>(s_row0) +
+                                          ((3 * (t.ntcap + 1) * 4 + 15) & ~15));
+    uint64_t* fmat = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(s_blk) + t.blkcap * 16);
+    uint64_t* fx = fmat + STAGES;
+    uint64_t* empty = fx + STAGES;
+    __shared__ double s_wss[NW];
+    __shared__ unsigned long long s_wmx[NW];
+    __shared__ long long s_k, s_klim, s_evals, s_outer, s_timeout, s_keval;
+    __shared__ int s_xb, s_phase, s_inner, s_test, s_done, s_start, s_skip, s_fail, s_dec_done;
+    __shared__ volatile int s_stop, s_epoch;
+    __shared__ double s_relres, s_res2, s_resinf;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tb = t.cta0[blockIdx.x], te = t.cta0[blockIdx.x + 1], nt = te - tb;
+    if (tid == 0) {
+        const volatile JacCtl* c = ctl;
+        s_k = c->k;
+        s_klim = c->k_limit;
+        s_evals = c->evals;
+        s_outer = c->outer;
+        s_timeout = c->timeout;
+        s_xb = c->xbuf;
+        s_phase = c->phase;
+        s_inner = c->inner < 2 ? 2 : c->inner;
+        s_test = c->test;
+        s_done = c->done;
+        s_skip = c->fault_skip_cta;
+        s_start = (c->done == DONE_RUNNING) && (c->status == 0) && nt <= t.ntcap;
+        s_relres = c->relres;
+        s_res2 = c->res2;
+        s_resinf = c->resinf;
+        s_keval = c->k_eval;
+        s_stop = 0;
+        s_epoch = 0;
+        s_fail = 0;
+        for (int q = 0; q < STAGES; ++q) {
+            mbar_init(&fmat[q], 1);
+            mbar_init(&fx[q], 1);
+            mbar_init(&empty[q], NW);
+        }
+        fence_mbar_init();
+    }
+    // the CTA's tile table (constant for the launch)
+    if (nt <= t.ntcap) {
+        const int bbase = __ldg(t.blk0 + tb);
+        for (int i = tid; i <= nt; i += blockDim.x) {
+            s_row0[i] = __ldg(t.row0 + tb + i);
+            s_nnz0[i] = __ldg(t.nnz0 + tb + i);
+            s_boff[i] = __ldg(t.blk0 + tb + i) - bbase;
+        }
+        const int nblk = __ldg(t.blk0 + te) - bbase;
+        const int4* gb = reinterpret_cast<const int4*>(t.blk) + bbase;
+        for (int i = tid; i < nblk && i < t.blkcap; i += blockDim.x) s_blk[i] = __ldg(gb + i);
+    }
+    __syncthreads();
+    if (!s_start) {
+        if (tid == 0 && nt > t.ntcap) atomicOr(&ctl->status, ST_TIMEOUT);
+        return;
+    }
+
+    int ksw = max_sweeps;
+    if (!MIXED && !s_test) {
+        const long long rem = s_klim - s_k;
+        ksw = (int)(rem < (long long)ksw ? (rem > 0 ? rem : 0) : ksw);
+    }
+    const long long njobs = (long long)ksw * nt;
+    const int inner = s_inner;
+    const int phase0 = s_phase;
+    const int xb0 = s_xb;
+    const int emax = t.emax;
+    const long long budget = s_timeout;
+
+    // ================================================= producer warp
+    if (warp == NW) {
+        if (lane == 0) {
+            const uint64_t pol = policy_evict_first();
+            long long jm = 0, jx = 0;
+            int fenced_sweep = 0;     // x of sweep 0 was written before this launch
+            long long t_last = clock64();
+            while (jx < njobs) {
+                bool prog = false;
+                // (A) constant tile data, as far ahead as the stages allow
+                if (jm < njobs) {
+                    const int sidx = (int)(jm % STAGES);
+                    const bool freed = jm < STAGES ||
+                                       mbar_try_wait(&empty[sidx], (unsigned)(((jm / STAGES) - 1) & 1));
+                    if (freed) {
+                        const int sw = (int)(jm / nt);
+                        const int i = (int)(jm - (long long)sw * nt);
+                        const int ph = phase_of(MIXED, MIXED ? (phase0 + sw) % inner : 0, inner);
+                        const bool fp64 = (ph == PH_P64 || ph == PH_P64R);
+                        unsigned char* st = smem + sidx * L.bytes;
+                        const int r0 = s_row0[i], r1 = s_row0[i + 1];
+                        const int p0 = s_nnz0[i], p1 = s_nnz0[i + 1];
+                        int* hdr = reinterpret_cast<int*>(st);
+                        hdr[0] = r0; hdr[1] = r1; hdr[2] = p0; hdr[3] = p1;
+                        const int4 h = s_blk[s_boff[i]];
+                        const bool over = (p1 - p0) > emax;
+                        unsigned bytes = 0;
+                        int vb = 0, ve = 0, cb = 0, ce = 0;
+                        if (!over) {
+                            if (fp64) { vb = p0 & ~1; ve = (p1 + 1) & ~1; bytes += (unsigned)(ve - vb) * 8u; }
+                            else { vb = p0 & ~3; ve = (p1 + 3) & ~3; bytes += (unsigned)(ve - vb) * 4u; }
+                            cb = p0 & ~3; ce = (p1 + 3) & ~3;
+                            bytes += (unsigned)(ce - cb) * 4u;
+                        }
+                        const int rb = r0 & ~3, re = (r1 + 1 + 3) & ~3;
+                        bytes += (unsigned)(re - rb) * 4u;
+                        const int hb = r0 & ~1, he = (r1 + 1) & ~1;
+                        if (fp64) bytes += 2u * (unsigned)(he - hb) * 8u;
+                        uint64_t* bar = &fmat[sidx];
+                        mbar_expect_tx(bar, bytes);
+                        // windowed tiles read tile-local columns, fallback tiles global ones
+                        const int* colsrc = (h.w & 1) ? m.col : t.lcol;
+                        if (!over) {
+                            if (ve > vb) {
+                                if (fp64) bulk_g2s(st + L.o_val, m.T64 + vb, (unsigned)(ve - vb) * 8u, bar, pol);
+                                else bulk_g2s(st + L.o_val, m.T32 + vb, (unsigned)(ve - vb) * 4u, bar, pol);
+                            }
+                            if (ce > cb) bulk_g2s(st + L.o_col, colsrc + cb, (unsigned)(ce - cb) * 4u, bar, pol);
+                        }
+                        bulk_g2s(st + L.o_rp, m.rowptr + rb, (unsigned)(re - rb) * 4u, bar, pol);
+                        if (fp64 && he > hb) {
+                            bulk_g2s(st + L.o_c, m.c + hb, (unsigned)(he - hb) * 8u, bar, pol);
+                            bulk_g2s(st + L.o_d, m.d + hb, (unsigned)(he - hb) * 8u, bar, pol);
+                        }
+                        ++jm;
+                        prog = true;
+                    }
+                }
+                // (B) x halo of the oldest claimed job whose sweep's x is complete
+                if (jx < jm) {
+                    const int sw = (int)(jx / nt);
+                    if (s_epoch >= sw) {
+                        if (sw > fenced_sweep) {
+                            // x of this sweep was written by other CTAs (generic proxy) before the
+                            // grid barrier; order those writes before our bulk (async-proxy) reads
+                            __threadfence();
+                            fence_proxy_async_global();
+                            fenced_sweep = sw;
+                        }
+                        const int sidx = (int)(jx % STAGES);
+                        const int i = (int)(jx - (long long)sw * nt);
+                        const int pos = MIXED ? (phase0 + sw) % inner : 0;
+                        const int ph = phase_of(MIXED, pos, inner);
+                        unsigned char* st = smem + sidx * L.bytes;
+                        const int4* blk = s_blk + s_boff[i];
+                        const int4 h = blk[0];
+                        uint64_t* bar = &fx[sidx];
+                        if (ph == PH_P64 || ph == PH_P64R) {
+                            const double* xsrc = MIXED ? v.x[xb0] : v.x[(xb0 + sw) & 1];
+                            mbar_expect_tx(bar, (unsigned)h.x * 8u);
+                            for (int q = 1; q <= h.z; ++q) {
+                                const int4 rn = blk[q];
+                                bulk_g2s(st + L.o_x + rn.z * 8, xsrc + rn.x, (unsigned)rn.y * 8u, bar, 0);
+                            }
+                        } else {
+                            const float* esrc = v.e[pos & 1];
+                            mbar_expect_tx(bar, (unsigned)h.x * 4u);
+                            for (int q = 1; q <= h.z; ++q) {
+                                const int4 rn = blk[q];
+                                bulk_g2s(st + L.o_x + rn.z * 4, esrc + rn.x, (unsigned)rn.y * 4u, bar, 0);
+                            }
+                        }
+                        ++jx;
+                        prog = true;
+                    }
+                }
+                if (prog) {
+                    t_last = clock64();
+                } else {
+                    if (s_stop) break;
+                    if (clock64() - t_last > budget) { atomicOr(&ctl->status, ST_TIMEOUT); break; }
+                }
+            }
+            // Drain: the copies of the last jobs must land before the CTA exits.
+            const long long t0 = clock64();
+            for (long long j = (jm > STAGES ? jm - STAGES : 0); j < jm; ++j) {
+                const unsigned par = (unsigned)((j / STAGES) & 1);
+                while (!mbar_try_wait(&fmat[(int)(j % STAGES)], par))
+                    if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); break; }
+                if (j < jx)
+                    while (!mbar_try_wait(&fx[(int)(j % STAGES)], par))
+                        if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); break; }
+            }
+        }
+        return;
+    }
+
+    // ================================================= math warps
+    long long k = s_k;
+    int xb = xb0, pos = phase0;
+    long long evals = s_evals, outer = s_outer;
+    long long jc = 0;
+    int nbar = 0;
+    unsigned long long tr_comp = 0, tr_wait = 0, tr_mark = (tid == 0) ? global_ns() : 0;
+    for (int sw = 0; sw < ksw; ++sw) {
+        const int ph = phase_of(MIXED, pos, inner);
+        const bool norm_ph = (ph == PH_P64 || ph == PH_P64R);
+        double ss = 0.0;
+        unsigned long long mx = 0;
+        const double* xs = v.x[xb];
+        double* xd = v.x[xb ^ 1];
+        const float* es = v.e[pos & 1];
+        float* ed = v.e[(pos + 1) & 1];
+        for (int i = 0; i < nt; ++i, ++jc) {
+            const int sidx = (int)(jc % STAGES);
+            const unsigned par = (unsigned)((jc / STAGES) & 1);
+            bool ok = true;
+            for (int w = 0; w < 2 && ok; ++w) {
+                uint64_t* bar = w == 0 ? &fmat[sidx] : &fx[sidx];
+                if (!mbar_try_wait(bar, par)) {
+                    if (s_fail) { ok = false; break; }
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(bar, par)) {
+                        if (s_fail || clock64() - t0 > budget) {
+                            if (!s_fail) atomicOr(&ctl->status, ST_TIMEOUT);
+                            s_fail = 1;
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+            }
+            if (ok) {
+                const unsigned char* st = smem + sidx * L.bytes;
+                const int r0 = s_row0[i], r1 = s_row0[i + 1], p0 = s_nnz0[i], p1 = s_nnz0[i + 1];
+                const int4 h = s_blk[s_boff[i]];
+                const bool over = (p1 - p0) > emax;
+                const bool win = !(h.w & 1);
+                const int r = r0 + tid;
+                const bool in = r < r1;
+                const int* srp = reinterpret_cast<const int*>(st + L.o_rp) - (r0 & ~3);
+                const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (p0 & ~3);
+                const int kb = in ? srp[r] : 0, ke = in ? srp[r + 1] : 0;
+                if (norm_ph) {
+                    const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
+                    const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
+                    const double* sd = reinterpret_cast<const double*>(st + L.o_d) - (r0 & ~1);
+                    const double* sx = reinterpret_cast<const double*>(st + L.o_x);
+                    double acc = in ? sc[r] : 0.0;
+                    double xi = 0.0;
+                    double a1[1] = {acc};
+                    const int kb1[1] = {kb}, len1[1] = {ke - kb};
+                    if (win) {
+                        xi = in ? sx[h.y + tid] : 0.0;
+                        rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; }, [&](int e) { return sx[scol[e]]; });
+                    } else {
+                        xi = in ? __ldcg(xs + r) : 0.0;
+                        if (!over)
+                            rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
+                                        [&](int e) { return __ldcg(xs + scol[e]); });
+                        else
+                            rows_dot<1>(a1, kb1, len1, [&](int e) { return __ldg(m.T64 + e); },
+                                        [&](int e) { return __ldcg(xs + __ldg(m.col + e)); });
+                    }
+                    acc = a1[0];
+                    if (in) {
+                        if (ph == PH_P64) {
+                            __stcg(xd + r, acc);
+                        } else {
+                            const float dl = (float)__dadd_rn(acc, -xi);
+                            __stcg(v.dlt + r, dl);
+                            __stcg(v.e[1] + r, dl);
+                        }
+                        accumulate_residual(acc, xi, sd[r], ss, mx);
+                    }
+                } else {
+                    const float* sv = reinterpret_cast<const float*>(st + L.o_val) - (p0 & ~3);
+                    const float* sx = reinterpret_cast<const float*>(st + L.o_x);
+                    float acc = in ? __ldcg(v.dlt + r) : 0.f;
+                    float a1[1] = {acc};
+                    const int kb1[1] = {kb}, len1[1] = {ke - kb};
+                    if (win)
+                        rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; }, [&](int e) { return sx[scol[e]]; });
+                    else if (!over)
+                        rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
+                                    [&](int e) { return __ldcg(es + scol[e]); });
+                    else
+                        rows_dot<1>(a1, kb1, len1, [&](int e) { return __ldg(m.T32 + e); },
+                                    [&](int e) { return __ldcg(es + __ldg(m.col + e)); });
+                    acc = a1[0];
+                    if (in) {
+                        if (ph == PH_P32) __stcg(ed + r, acc);
+                        else __stcg(v.x[xb] + r, __dadd_rn(__ldcg(v.x[xb] + r), (double)acc));
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[sidx]);
+        }
+        // ---- publish partial norms, grid barrier
+        if (norm_ph) {
+            const double ws = warp_sum(ss);
+            const unsigned long long wm = warp_max(mx);
+            if (lane == 0) { s_wss[warp] = ws; s_wmx[warp] = wm; }
+        }
+        consumer_sync<CT>();
+        if (tid == 0) {
+            const unsigned long long tb_ = global_ns();
+            tr_comp += tb_ - tr_mark;
+            tr_mark = tb_;
+            if (norm_ph) {
+                double b = 0.0;
+                unsigned long long bm = 0;
+                for (int w = 0; w < NW; ++w) { b += s_wss[w]; bm = umax64(bm, s_wmx[w]); }
+                Partial* slot = v.part + (sw & 1) * v.nslots + blockIdx.x;
+                __stcg(&slot->ss, b);
+                __stcg(&slot->mx, bm);
+            }
+            __threadfence();
+            if (!(s_skip == (int)blockIdx.x)) atomicAdd(&ctl->bar, 1ull);
+            const unsigned long long target = (unsigned long long)(nbar + 1) * gridDim.x;
+            const long long t0 = clock64();
+            while (ld_acquire_u64(&ctl->bar) < target) {
+                if (ld_volatile_i32(&ctl->status) & ST_TIMEOUT) { s_fail = 1; break; }
+                if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); s_fail = 1; break; }
+                __nanosleep(32);
+            }
+            {
+                const unsigned long long tc_ = global_ns();
+                tr_wait += tc_ - tr_mark;
+                tr_mark = tc_;
+            }
+            __threadfence();
+            if (!s_fail) s_epoch = nbar + 1;      // x of sweep nbar+1 is complete: the producer may copy it
+        }
+        ++nbar;
+        consumer_sync<CT>();
+        if (s_fail) break;
+        // ---- convergence decision (identical in every CTA)
+        if (norm_ph) {
+            if (warp == 0) {
+                double tss;
+                unsigned long long tmx;
+                reduce_partials_warp(v.part + (sw & 1) * v.nslots, gridDim.x, tss, tmx);
+                if (lane == 0) {
+                    const Decision d = decide(s_test, ctl->tol, s_klim, ctl->norm_kind, ctl->bnorm, tss, tmx, k);
+                    s_relres = d.relres;
+                    s_res2 = d.res2;
+                    s_resinf = d.resinf;
+                    s_keval = k;
+                    s_dec_done = d.done;
+                    if (d.numeric_bad && blockIdx.x == 0) atomicOr(&ctl->status, ST_NUMERIC);
+                    if (blockIdx.x == 0 && ctl->hist && evals < ctl->hist_cap) ctl->hist[evals] = d.relres;
+                }
+            }
+            consumer_sync<CT>();
+            evals += 1;
+            if (s_dec_done != DONE_RUNNING) { s_done = s_dec_done; break; }
+            if (ph == PH_P64) { k += 1; xb ^= 1; }
+            else pos = 1;
+        } else if (ph == PH_P32) {
+            pos += 1;
+        } else {   // PH_P32L
+            pos = 0;
+            k += inner;
+            outer += 1;
+        }
+        if (!MIXED && !s_test && k >= s_klim) break;
+    }
+    if (tid == 0 && v.trace) {
+        atomicAdd(v.trace + 4 * blockIdx.x + 0, tr_comp);
+        atomicAdd(v.trace + 4 * blockIdx.x + 1, tr_wait);
+        atomicAdd(v.trace + 4 * blockIdx.x + 2, (unsigned long long)nbar);
+    }
+    if (tid == 0) s_stop = 1;
+    if (blockIdx.x == 0 && tid == 0) {
+        ctl->k = k;
+        ctl->xbuf = xb;
+        ctl->phase = pos;
+        ctl->evals = evals;
+        ctl->outer = outer;
+        ctl->done = s_done;
+        ctl->relres = s_relres;
+        ctl->res2 = s_res2;
+        ctl->resinf = s_resinf;
+        ctl->k_eval = s_keval;
+        __threadfence();
+    }
+}
+
+template <int STAGES, bool MIXED>
+static const void* halo_fn()
+{
+    return reinterpret_cast<const void*>(&k_halo<STAGES, MIXED>);
+}
+
+const void* halo_kernel(int stages, bool mixed)
+{
+    if (stages == 3) return mixed ? halo_fn<3, true>() : halo_fn<3, false>();
+    if (stages == 4) return mixed ? halo_fn<4, true>() : halo_fn<4, false>();
+    return nullptr;
 }
 
 // =========================================================================
@@ -672,19 +1247,26 @@ cudaError_t launch_row_sweep(int ph, const DevMat& m, const DevVec& v, JacCtl* c
     return cudaGetLastError();
 }
 
-template <int RPT, int STAGES, bool MIXED>
+template <int RPT, int STAGES, bool MIXED, int NWM>
 static const void* persistent_fn()
 {
-    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED>);
+    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED, NWM>);
 }
 
+// rows = rows per tile = 32 x math warps: 224 -> 7 (2 CTAs/SM, 128 regs),
+// 256 -> 8 (2 CTAs/SM, 96 regs; or 3 stages, 72 regs, 3 CTAs/SM),
+// 480 -> 15 (1 CTA/SM, 128 regs).
 const void* persistent_kernel(int rows, int stages, bool mixed)
 {
-    if (rows == 256 && stages == 4) return mixed ? persistent_fn<1, 4, true>() : persistent_fn<1, 4, false>();
-    if (rows == 512 && stages == 4) return mixed ? persistent_fn<2, 4, true>() : persistent_fn<2, 4, false>();
-    if (rows == 512 && stages == 3) return mixed ? persistent_fn<2, 3, true>() : persistent_fn<2, 3, false>();
+    if (rows == 256 && stages == 3) return mixed ? persistent_fn<1, 3, true, 8>() : persistent_fn<1, 3, false, 8>();
+    if (stages != 4) return nullptr;
+    if (rows == 224) return mixed ? persistent_fn<1, 4, true, 7>() : persistent_fn<1, 4, false, 7>();
+    if (rows == 256) return mixed ? persistent_fn<1, 4, true, 8>() : persistent_fn<1, 4, false, 8>();
+    if (rows == 480) return mixed ? persistent_fn<1, 4, true, 15>() : persistent_fn<1, 4, false, 15>();
     return nullptr;
 }
+
+int persistent_threads(int rows) { return rows + 32; }
 
 cudaError_t launch_persistent(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
                               const DevTiles& t, JacCtl* ctl, int max_sweeps, cudaStream_t s)

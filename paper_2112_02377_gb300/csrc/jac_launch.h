@@ -13,6 +13,9 @@ cudaError_t launch_row_sweep(int phase, const DevMat& m, const DevVec& v, JacCtl
 // nullptr if that combination is not compiled.
 const void* persistent_kernel(int rows, int stages, bool mixed);
 int persistent_smem_bytes(int rows, int emax, int stages);
+int persistent_threads(int rows);
+const void* halo_kernel(int stages, bool mixed);
+int halo_smem_bytes(int rows, int emax, int xcap, int ntcap, int blkcap, int stages);
 cudaError_t launch_persistent(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
                               const DevTiles& t, JacCtl* ctl, int max_sweeps, cudaStream_t s);
 

@@ -288,4 +288,70 @@ void make_tiling(const TForm& tf, const Plan& plan, int32_t rows_per_tile, int32
     t.cta0[ctas] = (int32_t)nt;
 }
 
+void make_windows(const TForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w)
+{
+    const int64_t nt = t.ntiles();
+    const int64_t GAP = 16;     // columns closer than this join one run
+    w = Windows();
+    w.xcap = xcap;
+    w.maxruns = maxruns;
+    w.blk0.resize(nt + 1);
+    w.lcol.assign(tf.col.size(), 0);
+    std::vector<int32_t> cols;
+    struct Run { int64_t s, e; };   // [s, e) aligned to 4
+    std::vector<Run> runs;
+    for (int64_t ti = 0; ti < nt; ++ti) {
+        const int64_t r0 = t.row0[ti], r1 = t.row0[ti + 1];
+        const int64_t p0 = tf.rowptr[r0], p1 = tf.rowptr[r1];
+        w.blk0[ti] = (int32_t)(w.blk.size() / 4);
+        cols.assign(tf.col.begin() + p0, tf.col.begin() + p1);
+        for (int64_t r = r0; r < r1; ++r) cols.push_back((int32_t)r);
+        std::sort(cols.begin(), cols.end());
+        cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+        runs.clear();
+        for (int32_t c : cols) {
+            const int64_t a = (int64_t)c & ~(int64_t)3;
+            if (!runs.empty() && a <= runs.back().e + GAP) {
+                runs.back().e = std::max<int64_t>(runs.back().e, ((int64_t)c + 4) & ~(int64_t)3);
+            } else {
+                runs.push_back({a, ((int64_t)c + 4) & ~(int64_t)3});
+            }
+        }
+        int64_t xlen = 0;
+        for (auto& rn : runs) xlen += rn.e - rn.s;
+        const bool fb = (p1 - p0) > emax || xlen > xcap || (int64_t)runs.size() > maxruns;
+        int64_t own = 0;
+        if (!fb) {
+            int64_t off = 0;
+            for (auto& rn : runs) {
+                if (r0 >= rn.s && r0 < rn.e) own = off + (r0 - rn.s);
+                off += rn.e - rn.s;
+            }
+            // local column of every entry: offset of its run + position in the run
+            for (int64_t k = p0; k < p1; ++k) {
+                const int64_t c = tf.col[k];
+                int64_t lo = 0, hi = (int64_t)runs.size() - 1, o2 = 0;
+                while (lo < hi) {               // last run with s <= c
+                    int64_t mid = (lo + hi + 1) / 2;
+                    if (runs[mid].s <= c) lo = mid;
+                    else hi = mid - 1;
+                }
+                for (int64_t q = 0; q < lo; ++q) o2 += runs[q].e - runs[q].s;
+                w.lcol[k] = (int32_t)(o2 + (c - runs[lo].s));
+            }
+            w.window_elems += xlen;
+        } else {
+            ++w.fallback_tiles;
+        }
+        const int32_t nr = fb ? 0 : (int32_t)runs.size();
+        w.blk.insert(w.blk.end(), {(int32_t)(fb ? 0 : xlen), (int32_t)own, nr, fb ? TILE_FALLBACK : 0});
+        int64_t dst = 0;
+        for (int32_t q = 0; q < nr; ++q) {
+            w.blk.insert(w.blk.end(), {(int32_t)runs[q].s, (int32_t)(runs[q].e - runs[q].s), (int32_t)dst, 0});
+            dst += runs[q].e - runs[q].s;
+        }
+    }
+    w.blk0[nt] = (int32_t)(w.blk.size() / 4);
+}
+
 }  // namespace jac

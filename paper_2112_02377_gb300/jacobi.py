@@ -31,7 +31,8 @@ _STATUS_NAMES = ["JAC_OK", "JAC_EINVAL", "JAC_ENOMEM", "JAC_ECUDA", "JAC_ESINGUL
 # Symbols declared in include/jacobi.h (checked by the CPU test suite).
 EXPORTED = ["jac_opts_default", "jac_setup", "jac_setup_batched", "jac_set_x", "jac_set_b", "jac_sweep",
             "jac_solve", "jac_get_x", "jac_get_history", "jac_get_batch_results", "jac_adjoint_grad",
-            "jac_stats", "jac_partition_plan", "jac_dependency_lists", "jac_last_error", "jac_free"]
+            "jac_stats", "jac_partition_plan", "jac_dependency_lists", "jac_last_error", "jac_free",
+            "jac_get_trace"]
 
 
 class JacobiError(RuntimeError):
@@ -51,7 +52,8 @@ class jac_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("norm", ctypes.c_int32), ("sweeps_per_graph", ctypes.c_int32),
                 ("inner_sweeps", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("subdomains", ctypes.c_int32 * 3),
                 ("node_of_row", ctypes.c_void_p), ("nrhs", ctypes.c_int32), ("transpose", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("history", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("history", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("timeout_cycles", ctypes.c_uint64),
                 ("fault_skip_cta", ctypes.c_int32), ("device", ctypes.c_int32)]
 
@@ -59,7 +61,8 @@ class jac_opts(ctypes.Structure):
 class jac_stats_t(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("n", "nnz", "nparts", "interface_rows", "ntiles", "ctas",
                                                 "halo_entries", "max_row", "k", "sweeps_total",
-                                                "outer_iterations")] + \
+                                                "outer_iterations", "halo_fallback_tiles",
+                                                "halo_window_elems")] + \
                [(f, ctypes.c_double) for f in ("last_relres", "last_res2", "last_resinf", "last_ms",
                                                  "bytes_per_sweep_fp64", "bytes_per_sweep_fp32")] + \
                [(f, ctypes.c_int32) for f in ("variant", "precision", "splitting", "nrhs")]
@@ -105,6 +108,7 @@ def lib(build_if_needed: bool = True):
                 "jac_get_batch_results": (I32, [P, P, P]),
                 "jac_adjoint_grad": (I32, [P, P, P, P, I32]),
                 "jac_stats": (I32, [P, P]),
+                "jac_get_trace": (I32, [P, P, P, I64, P]),
                 "jac_partition_plan": (I32, [P, I32, I32, P, P, P, P]),
                 "jac_dependency_lists": (I32, [P, I32, I32, P, P, P, P, P]),
                 "jac_last_error": (ctypes.c_char_p, [P]),
@@ -263,6 +267,18 @@ def jac_adjoint_grad(ctx, lam, x, dA):
         raise ValueError("lambda, x and dA must live in the same memory")
     _check(lib().jac_adjoint_grad(ctx, lp, xp, gp, lm), ctx)
     return dA
+
+
+def jac_get_trace(ctx):
+    """Per-CTA (compute_ms, wait_ms) arrays of the last sweep/solve call."""
+    n = ctypes.c_int64()
+    _check(lib().jac_get_trace(ctx, None, None, 0, ctypes.byref(n)), ctx)
+    comp = np.zeros(n.value)
+    wait = np.zeros(n.value)
+    if n.value:
+        _check(lib().jac_get_trace(ctx, ctypes.c_void_p(comp.ctypes.data), ctypes.c_void_p(wait.ctypes.data),
+                                   n.value, ctypes.byref(n)), ctx)
+    return comp, wait
 
 
 def jac_stats(ctx) -> dict:

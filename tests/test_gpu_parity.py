@@ -69,7 +69,7 @@ def _cases():
 
 
 @pytest.mark.parametrize("name,A,b", list(_cases()))
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_per_sweep_parity_and_splitting_invariance(name, A, b, variant):
     rng = np.random.default_rng(1)
     x0 = rng.uniform(-1, 1, A.n)
@@ -100,7 +100,8 @@ def test_per_sweep_parity_and_splitting_invariance(name, A, b, variant):
 @pytest.mark.parametrize("name,A,b", list(_cases())[:2])
 def test_variants_and_graph_batching_are_bit_identical(name, A, b):
     outs = []
-    for variant, K, rows in [(1, 64, 256), (2, 64, 256), (2, 7, 256), (2, 1, 256), (2, 64, 512), (2, 5, 512)]:
+    for variant, K, rows in [(1, 64, 256), (2, 64, 256), (2, 7, 256), (2, 1, 256), (2, 64, 480), (2, 5, 480),
+                             (2, 64, 224), (3, 64, 256), (3, 3, 256), (3, 1, 256)]:
         ctx = _setup(A, b, "bandrow", 3, variant=variant, sweeps_per_graph=K, tile_rows=rows)
         try:
             J.jac_sweep(ctx, 23)
@@ -119,7 +120,7 @@ def test_variants_and_graph_batching_are_bit_identical(name, A, b):
         assert np.array_equal(o, outs[0])
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("split,P", SPLITS)
 def test_config1_solve_16cubed_to_1e6(variant, split, P):
     """16^3 7-point Laplace, b = A x* (seed 0), x0 = 0, relative residual 1e-6:
@@ -142,7 +143,7 @@ def test_config1_solve_16cubed_to_1e6(variant, split, P):
         J.jac_free(ctx)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_paper_q1_count_with_inf_norm(variant):
     """The paper's cube-35937 run: 746 iterations to ||r||_inf < 1e-8 (Sec. 5.2)."""
     A, b = W.q1_laplace(33)
@@ -183,7 +184,7 @@ def test_one_by_one_and_diagonal_systems():
     d = np.random.default_rng(3).uniform(1, 2, 700)
     A = W.dense_to_csr(np.diag(d))
     b = np.random.default_rng(4).uniform(-1, 1, 700)
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         ctx = _setup(A, b, "bandrow", 7, variant=variant)
         try:
             k, rel, st = J.jac_solve(ctx, 0.0, 5)
@@ -270,7 +271,7 @@ def test_errors_singular_duplicate_diagonal_divergence():
     assert ei.value.status == J.JAC_EINVAL
     # rho(T) >> 1: the iterate overflows and the residual becomes Inf/NaN
     D = np.array([[1e-200, 1.0, 0.0], [1.0, 1e-200, 1.0], [0.0, 1.0, 1e-200]])
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         ctx = J.jac_setup(W.dense_to_csr(D), np.ones(3), J.JAC_BANDROW, 1, J.opts(variant=variant))
         try:
             with pytest.raises(J.JacobiError) as ei:
@@ -285,13 +286,14 @@ def test_grid_barrier_timeout_is_reported_and_recoverable():
     give up after a short bounded wait and the call reports JAC_ETIMEOUT."""
     A = W.laplace7(24)
     xs, b = W.solution_and_rhs(A, 0)
-    ctx = J.jac_setup(A, b, J.JAC_BANDROW, 4, J.opts(variant=2, fault_skip_cta=1, timeout_cycles=20_000_000))
-    try:
-        with pytest.raises(J.JacobiError) as ei:
-            J.jac_sweep(ctx, 5)
-        assert ei.value.status == J.JAC_ETIMEOUT
-    finally:
-        J.jac_free(ctx)
+    for variant in (2, 3):
+        ctx = J.jac_setup(A, b, J.JAC_BANDROW, 4, J.opts(variant=variant, fault_skip_cta=1, timeout_cycles=20_000_000))
+        try:
+            with pytest.raises(J.JacobiError) as ei:
+                J.jac_sweep(ctx, 5)
+            assert ei.value.status == J.JAC_ETIMEOUT
+        finally:
+            J.jac_free(ctx)
     ctx = _setup(A, b, "bandrow", 4, variant=2)
     try:
         J.jac_sweep(ctx, 5)
@@ -306,7 +308,7 @@ def test_grid_barrier_timeout_is_reported_and_recoverable():
 
 # ---------------------------------------------------- mixed precision ----
 
-@pytest.mark.parametrize("variant,rows", [(1, 256), (2, 256), (2, 512)])
+@pytest.mark.parametrize("variant,rows", [(1, 256), (2, 256), (2, 224), (2, 480), (3, 256)])
 def test_mixed_precision_reaches_1e10(variant, rows):
     A = W.laplace7(16)
     xs, b = W.solution_and_rhs(A, 0)
@@ -343,8 +345,9 @@ def test_full_size_160cubed_per_sweep_parity_all_splittings(big):
     x0 = rng.uniform(-1, 1, A.n)
     Mo = O.prepare(A)
     finals = []
-    for split, P in [("bandrow", 64), ("bandrow_nnz", 64), ("substruct", 0)]:
-        ctx = _setup(A, b, split, P, variant=2, sub=(4, 4, 4))
+    for (split, P), variant in [(("bandrow", 64), 3), (("bandrow_nnz", 64), 3), (("substruct", 0), 3),
+                                (("bandrow", 64), 2)]:
+        ctx = _setup(A, b, split, P, variant=variant, sub=(4, 4, 4))
         try:
             J.jac_set_x(ctx, x0)
             x = x0
