@@ -284,6 +284,39 @@ jac_status jac_partition_plan(const jac_csr* A, jac_splitting s, int32_t nparts,
 jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t nparts, const jac_opts* o,
                                 int64_t* recv_ptr, int32_t* recv_from, int64_t* recv, int64_t* total);
 
+/*
+ * jac_sweep_noalloc -- k synchronous Jacobi sweeps that allocate no memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need a solve -- code running under
+ * a memory pool that owns the device, loops that must not stall on the device
+ * synchronisation cudaMalloc/cudaFree imply, or host applications that forbid
+ * allocation after start-up.  It uses only the caller's buffers and a fixed
+ * scratch area compiled into the library (JAC_NOALLOC_SCRATCH_BYTES, held on
+ * every GPU that loads the library until the process exits); it calls no
+ * allocator, the CUDA runtime's or any library's.
+ *   n          rows, 1 <= n <= JAC_NOALLOC_MAX_ROWS (larger n: JAC_EINVAL).
+ *   rowptr, col, val   0-based CSR of A in device memory, diagonal stored in
+ *              every row (a zero or missing diagonal returns JAC_ENUMERIC).
+ *   b, x_in    device vectors of n doubles; x_out receives x^k (n doubles,
+ *              must not alias x_in).  k >= 0 sweeps (k = 0 copies x_in).
+ *   relres_out (host, may be NULL) ||b - A x^{k-1}||_2 / ||b||_2 of the last
+ *              pre-update iterate (left unchanged when k = 0).
+ *   stream     cudaStream_t (NULL = legacy default stream); the call
+ *              synchronises it before returning.
+ * Each sweep computes x'_i = (b_i - sum_{j != i} a_ij x_j) / a_ii with one
+ * launch, as the one-launch-per-sweep variant does.  The first call on a
+ * device looks up the scratch area's device address (make it before any
+ * stream capture).  All calls share the scratch area: calls whose work
+ * overlaps on the GPU race.  Errors: JAC_EINVAL, JAC_ENUMERIC, JAC_ECUDA;
+ * jac_last_error(NULL) describes the last failure on this thread.
+ */
+#define JAC_NOALLOC_MAX_ROWS 4194304
+#define JAC_NOALLOC_SCRATCH_BYTES 33816640
+jac_status jac_sweep_noalloc(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                             const double* b, const double* x_in, double* x_out, int32_t k,
+                             double* relres_out, void* stream);
+
 /* Message of the last failure on ctx (NULL ctx: last jac_setup* failure on
  * this thread).  Never NULL; valid until the next call on ctx. */
 const char* jac_last_error(const jac_ctx* ctx);

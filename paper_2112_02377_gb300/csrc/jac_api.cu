@@ -18,6 +18,11 @@ using namespace jac;
 
 static thread_local std::string g_setup_error = "no error";
 
+namespace jac {
+// Message for jac_last_error(NULL) from calls that have no context.
+void record_thread_error(const std::string& msg) { g_setup_error = msg; }
+}  // namespace jac
+
 struct jac_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -32,7 +32,7 @@ _STATUS_NAMES = ["JAC_OK", "JAC_EINVAL", "JAC_ENOMEM", "JAC_ECUDA", "JAC_ESINGUL
 EXPORTED = ["jac_opts_default", "jac_setup", "jac_setup_batched", "jac_set_x", "jac_set_b", "jac_sweep",
             "jac_solve", "jac_get_x", "jac_get_history", "jac_get_batch_results", "jac_adjoint_grad",
             "jac_stats", "jac_partition_plan", "jac_dependency_lists", "jac_last_error", "jac_free",
-            "jac_get_trace"]
+            "jac_get_trace", "jac_sweep_noalloc"]
 
 
 class JacobiError(RuntimeError):
@@ -109,6 +109,7 @@ def lib(build_if_needed: bool = True):
                 "jac_adjoint_grad": (I32, [P, P, P, P, I32]),
                 "jac_stats": (I32, [P, P]),
                 "jac_get_trace": (I32, [P, P, P, I64, P]),
+                "jac_sweep_noalloc": (I32, [I64, P, P, P, P, P, P, I32, P, P]),
                 "jac_partition_plan": (I32, [P, I32, I32, P, P, P, P]),
                 "jac_dependency_lists": (I32, [P, I32, I32, P, P, P, P, P]),
                 "jac_last_error": (ctypes.c_char_p, [P]),
@@ -328,6 +329,28 @@ def jac_dependency_lists(A, splitting: int, nparts: int, o: Optional[jac_opts] =
                                   ctypes.c_void_p(recv.ctypes.data), ctypes.byref(tot)), None)
     o.node_of_row = None
     return rptr, rfrom[: tot.value], recv[: tot.value]
+
+
+def jac_sweep_noalloc(rowptr, col, val, b, x_in, x_out, k: int, stream=None) -> float:
+    """k sweeps without any allocation inside the library (device tensors in,
+    x^k written to x_out).  Returns the relres of the last pre-update iterate
+    (NaN when k == 0)."""
+    ptrs = []
+    for a, dt, nm in ((rowptr, np.int32, "rowptr"), (col, np.int32, "col"), (val, np.float64, "val"),
+                      (b, np.float64, "b"), (x_in, np.float64, "x_in")):
+        p, m, keep = _buf(a, dt, nm)
+        if m != JAC_MEM_DEVICE:
+            raise ValueError(f"{nm} must be in device memory")
+        ptrs.append((p, keep))
+    po, mo, ko = _buf(x_out, np.float64, "x_out", writable=True)
+    if mo != JAC_MEM_DEVICE:
+        raise ValueError("x_out must be in device memory")
+    rel = ctypes.c_double(float("nan"))
+    n = len(rowptr) - 1
+    st = lib().jac_sweep_noalloc(n, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[4][0], po, int(k),
+                                 ctypes.byref(rel), ctypes.c_void_p(int(stream) if stream else 0))
+    _check(st, None)
+    return rel.value
 
 
 def jac_last_error(ctx=None) -> str:
