@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjacobi_gb300.so")
-SOURCES = ["jac_kernels.cu", "jac_api.cu", "jac_partition.cpp", "jac_noalloc.cu"]
+SOURCES = ["jac_kernels.cu", "jac_api.cu", "jac_partition.cpp", "jac_noalloc.cu", "jac_batched.cu"]
 HEADERS = ["jac_device.cuh", "jac_internal.h", "jac_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -71,6 +72,28 @@ struct jac_ctx {
     cudaGraphExec_t g64 = nullptr, gmix = nullptr;
     bool no_graph = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // batched contexts
+    bool batched = false;
+    int nsys = 0, npairs = 0;
+    const void* bfn = nullptr;
+    int* d_tile_sys = nullptr;
+    int* d_sys_pair0 = nullptr;
+    int* d_cta_pair0 = nullptr;
+    int* d_cta_sys0 = nullptr;
+    double* d_bnorm = nullptr;
+    unsigned* d_cnt = nullptr;
+    int* d_mask = nullptr;
+    long long* d_ksys = nullptr;
+    int* d_kpar = nullptr;
+    double* d_rel = nullptr;
+    int* d_sys_status = nullptr;
+    unsigned* d_ndone = nullptr;
+    double* d_pss = nullptr;
+    unsigned long long* d_pmx = nullptr;
+    int* d_row_sys = nullptr;
+    long long* d_sys_off = nullptr;
+    double* d_bstage = nullptr;      // n*nrhs staging for batched rhs / x
+    std::vector<long long> h_sys_off;
     // host-side bookkeeping
     int64_t sweeps_total = 0, outer_last = 0;
     double last_ms = 0.0;
@@ -197,10 +220,38 @@ DevTiles devtiles(const jac_ctx* c)
     return t;
 }
 
+DevBatch devbatch(const jac_ctx* c)
+{
+    DevBatch b;
+    b.nsys = c->nsys;
+    b.npairs = c->npairs;
+    b.tile_sys = c->d_tile_sys;
+    b.sys_pair0 = c->d_sys_pair0;
+    b.cta_pair0 = c->d_cta_pair0;
+    b.cta_sys0 = c->d_cta_sys0;
+    b.bnorm = c->d_bnorm;
+    b.cnt = c->d_cnt;
+    b.mask = c->d_mask;
+    b.ksys = c->d_ksys;
+    b.kpar = c->d_kpar;
+    b.rel = c->d_rel;
+    b.sys_status = c->d_sys_status;
+    b.ndone = c->d_ndone;
+    b.pss = c->d_pss;
+    b.pmx = c->d_pmx;
+    return b;
+}
+
 // Enqueue one "graph step": K sweeps (FP64) or one refinement cycle block (mixed).
 jac_status enqueue_step(jac_ctx* c, bool mixed)
 {
     cudaStream_t s = stream_of(c);
+    if (c->batched) {
+        CK(c, launch_reset_bar(c->d_ctl, s));
+        CK(c, launch_batched(mixed ? c->pfnmix : c->pfn64, c->grid, c->threads, c->smem, devmat(c), devvec(c),
+                             devtiles(c), devbatch(c), c->d_ctl, c->K, s));
+        return JAC_OK;
+    }
     if (c->variant >= 2) {
         CK(c, launch_reset_bar(c->d_ctl, s));
         CK(c, launch_persistent(mixed ? c->pfnmix : c->pfn64, c->grid, c->threads, c->smem, devmat(c), devvec(c),
@@ -272,6 +323,21 @@ jac_status run_graph(jac_ctx* c, bool mixed)
     return JAC_OK;
 }
 
+// Batched: gather each right-hand side's current iterate (some stopped ones
+// live in the other ping-pong buffer) into x[0], restart k at 0 and re-arm
+// every system's test.
+jac_status batched_restart(jac_ctx* c)
+{
+    cudaStream_t s = stream_of(c);
+    CK(c, launch_batched_gather_x(c->d_x[0], c->d_x[1], c->d_row_sys, c->d_mask, c->d_kpar, c->h_ctl[0].xbuf & 1,
+                                  c->n, c->nrhs, c->d_bstage, s));
+    CK(c, cudaMemcpyAsync(c->d_x[0], c->d_bstage, (size_t)c->n * c->nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(c, launch_batched_reset(devbatch(c), c->nrhs, s));
+    CK(c, launch_reset_iterate(c->d_ctl, s));
+    c->h_ctl[0].xbuf = 0;
+    return JAC_OK;
+}
+
 jac_status status_from_ctl(jac_ctx* c, const JacCtl& h)
 {
     if (h.status & ST_TIMEOUT)
@@ -311,6 +377,9 @@ void destroy(jac_ctx* c)
     dfree(c->d_part); dfree(c->d_ctl); dfree(c->d_hist); dfree(c->d_perm); dfree(c->d_stage); dfree(c->d_stage2);
     dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0); dfree(c->d_cta0);
     dfree(c->d_blk0); dfree(c->d_blk); dfree(c->d_lcol); dfree(c->d_trace);
+    dfree(c->d_tile_sys); dfree(c->d_sys_pair0); dfree(c->d_cta_pair0); dfree(c->d_cta_sys0); dfree(c->d_bnorm);
+    dfree(c->d_cnt); dfree(c->d_mask); dfree(c->d_ksys); dfree(c->d_kpar); dfree(c->d_rel); dfree(c->d_sys_status);
+    dfree(c->d_ndone); dfree(c->d_pss); dfree(c->d_pmx); dfree(c->d_row_sys); dfree(c->d_sys_off); dfree(c->d_bstage);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     delete c;
 }
@@ -683,12 +752,225 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     return JAC_OK;
 }
 
-jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const* b, const jac_opts* o,
+jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const* b, const jac_opts* o_in,
                              jac_ctx** out)
 {
-    (void)nsys; (void)A; (void)b; (void)o;
-    if (out) *out = nullptr;
-    return fail(nullptr, JAC_EINVAL, "jac_setup_batched: not available in this build");
+    if (!out) return fail(nullptr, JAC_EINVAL, "out is NULL");
+    *out = nullptr;
+    jac_opts o;
+    jac_opts_default(&o);
+    if (o_in) o = *o_in;
+    if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
+    const int nrhs = o.nrhs;
+    if (nrhs != 1 && nrhs != 2 && nrhs != 4) return fail(nullptr, JAC_EINVAL, "batched: opts.nrhs must be 1, 2 or 4");
+    {
+        jac_opts chk = o;
+        chk.nrhs = 1;
+        jac_status st = check_opts(chk, nullptr);
+        if (st != JAC_OK) return st;
+    }
+    if (nsys < 1 || nsys > 65536 || !A) return fail(nullptr, JAC_EINVAL, "batched: need 1 <= nsys <= 65536 systems");
+    const int memory = A[0].memory;
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, JAC_ECUDA, "no CUDA device");
+    DeviceGuard guard(dev);
+
+    // ---- pack the systems block-diagonally in iteration-matrix form
+    TForm big;
+    big.rowptr.push_back(0);
+    std::vector<long long> off(nsys + 1, 0);
+    for (int s = 0; s < nsys; ++s) {
+        if (A[s].memory != memory) return fail(nullptr, JAC_EINVAL, "batched: all systems must use the same memory");
+        HostView hv;
+        jac_status st = host_view(&A[s], hv, nullptr);
+        if (st != JAC_OK) return st;
+        HostCSR M;
+        Error e = host_csr_from_abi(&hv.csr, o.transpose != 0, M);
+        if (!e.ok()) return fail(nullptr, e.st, "system " + std::to_string(s) + ": " + e.msg);
+        Plan p1;
+        e = make_plan(M, JAC_BANDROW, 1, o, p1);
+        TForm tf;
+        if (e.ok()) e = make_tform(M, p1, tf);
+        if (!e.ok()) return fail(nullptr, e.st, "system " + std::to_string(s) + ": " + e.msg);
+        const long long base = off[s], ebase = big.rowptr.back();
+        if (base + M.n > INT32_MAX - 64 || ebase + (long long)tf.col.size() > INT32_MAX - 64)
+            return fail(nullptr, JAC_EINVAL, "batched: packed system exceeds 2^31 rows or entries");
+        for (int64_t r = 0; r < M.n; ++r) big.rowptr.push_back((int32_t)(ebase + tf.rowptr[r + 1]));
+        for (size_t q = 0; q < tf.col.size(); ++q) big.col.push_back((int32_t)(tf.col[q] + base));
+        big.T.insert(big.T.end(), tf.T.begin(), tf.T.end());
+        big.d.insert(big.d.end(), tf.d.begin(), tf.d.end());
+        big.max_off = std::max(big.max_off, tf.max_off);
+        off[s + 1] = base + M.n;
+    }
+    const int64_t n = off[nsys];
+    big.n = n;
+    const int64_t nnz_off = big.rowptr[n];
+    Plan plan;
+    plan.part_ptr.assign(off.begin(), off.end());
+    plan.perm.resize(n);
+    std::iota(plan.perm.begin(), plan.perm.end(), 0);
+    plan.iperm = plan.perm;
+
+    std::unique_ptr<jac_ctx, void (*)(jac_ctx*)> c(new jac_ctx(), destroy);
+    jac_ctx* C = c.get();
+    c->device = dev;
+    c->stream = (cudaStream_t)o.stream;
+    c->o = o;
+    c->batched = true;
+    c->nsys = nsys;
+    c->nrhs = nrhs;
+    c->n = n;
+    c->nnz = nnz_off + n;
+    c->nnz_off = nnz_off;
+    c->max_off = big.max_off;
+    c->max_row = big.max_off + 1;
+    c->splitting = JAC_BANDROW;
+    c->precision = o.precision;
+    c->nparts = nsys;
+    c->K = o.sweeps_per_graph;
+    c->variant = 2;
+    c->h_sys_off = off;
+
+    // ---- launch configuration: 7 math warps + producer, 2 CTAs/SM, 4 stages
+    cudaDeviceProp prop;
+    CK(nullptr, cudaGetDeviceProperties(&prop, dev));
+    const int rows = batched_rows();
+    c->rows_per_tile = rows;
+    c->stages = 4;
+    {
+        const int64_t cap_entries = std::max<int64_t>(1, big.max_off) * rows;
+        const int64_t budget = 27 * 1024 - (int64_t)rows * (4 + 8 * nrhs + 8) - 1024;
+        c->emax = (int)std::min<int64_t>(cap_entries, std::max<int64_t>(rows, budget / 12));
+    }
+    c->pfn64 = batched_kernel(nrhs, false);
+    c->pfnmix = batched_kernel(nrhs, true);
+    c->smem = batched_smem_bytes(rows, c->emax, nrhs, c->stages);
+    c->threads = batched_threads();
+    int per_sm = 0;
+    {
+        CK(nullptr, cudaFuncSetAttribute(c->pfn64, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
+        CK(nullptr, cudaFuncSetAttribute(c->pfnmix, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
+        int a1 = 0, a2 = 0;
+        CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a1, c->pfn64, c->threads, c->smem));
+        CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, c->pfnmix, c->threads, c->smem));
+        per_sm = std::min(std::min(a1, a2), 2);
+    }
+    if (per_sm < 1) return fail(nullptr, JAC_EINVAL, "batched kernel cannot be made co-resident");
+    c->grid = per_sm * prop.multiProcessorCount;
+    Tiling tl;
+    make_tiling(big, plan, rows, c->emax, c->grid, tl);
+    c->ntiles = (int)tl.ntiles();
+    // (CTA, system) partial slots: pairs ordered by CTA then system; the slots
+    // of one system are contiguous because CTAs own contiguous tile ranges.
+    std::vector<int32_t> cta_pair0(c->grid, 0), cta_sys0(c->grid, 0), sys_pair0(nsys + 1, -1);
+    int npairs = 0, last_sys = -1;
+    for (int g = 0; g < c->grid; ++g) {
+        cta_pair0[g] = npairs;
+        const int tb = tl.cta0[g], te = tl.cta0[g + 1];
+        if (tb == te) continue;
+        const int s0 = tl.tile_part[tb], s1 = tl.tile_part[te - 1];
+        cta_sys0[g] = s0;
+        for (int s = s0; s <= s1; ++s, ++npairs) {
+            if (sys_pair0[s] < 0) sys_pair0[s] = npairs;
+            else if (s != last_sys) return fail(nullptr, JAC_ECUDA, "batched: internal tiling error");
+            last_sys = s;
+        }
+    }
+    sys_pair0[nsys] = npairs;
+    for (int s = 0; s < nsys; ++s)
+        if (sys_pair0[s] < 0) return fail(nullptr, JAC_ECUDA, "batched: a system has no tile");
+    c->npairs = npairs;
+    c->nslots = c->grid;
+
+    // ---- device memory
+    const size_t nv = (size_t)n * nrhs;
+    CK(nullptr, dalloc(&c->d_rowptr, n + 1 + 16));
+    CK(nullptr, dalloc(&c->d_col, nnz_off + 16));
+    CK(nullptr, dalloc(&c->d_T64, nnz_off + 16));
+    CK(nullptr, dalloc(&c->d_c, nv + 16 * nrhs));
+    CK(nullptr, dalloc(&c->d_d, n + 16));
+    CK(nullptr, dalloc(&c->d_x[0], nv + 16 * nrhs));
+    CK(nullptr, dalloc(&c->d_x[1], nv + 16 * nrhs));
+    if (o.precision == JAC_MIXED) {
+        CK(nullptr, dalloc(&c->d_T32, nnz_off + 16));
+        CK(nullptr, dalloc(&c->d_e[0], nv + 16 * nrhs));
+        CK(nullptr, dalloc(&c->d_e[1], nv + 16 * nrhs));
+        CK(nullptr, dalloc(&c->d_dlt, nv + 16 * nrhs));
+    }
+    CK(nullptr, dalloc(&c->d_part, 2 * (size_t)c->nslots + 2));
+    CK(nullptr, dalloc(&c->d_ctl, 1));
+    CK(nullptr, dalloc(&c->d_bstage, nv + 16));
+    CK(nullptr, cudaMallocHost((void**)&c->h_ctl, 2 * sizeof(JacCtl)));
+    std::memset(c->h_ctl, 0, 2 * sizeof(JacCtl));
+    CK(nullptr, cudaEventCreate(&c->ev0));
+    CK(nullptr, cudaEventCreate(&c->ev1));
+    CK(nullptr, dalloc(&c->d_row0, tl.row0.size()));
+    CK(nullptr, dalloc(&c->d_nnz0, tl.nnz0.size()));
+    CK(nullptr, dalloc(&c->d_cta0, tl.cta0.size()));
+    CK(nullptr, dalloc(&c->d_tile_sys, tl.tile_part.size() + 1));
+    CK(nullptr, dalloc(&c->d_sys_pair0, (size_t)nsys + 1));
+    CK(nullptr, dalloc(&c->d_cta_pair0, (size_t)c->grid));
+    CK(nullptr, dalloc(&c->d_cta_sys0, (size_t)c->grid));
+    CK(nullptr, dalloc(&c->d_bnorm, (size_t)nsys * nrhs));
+    CK(nullptr, dalloc(&c->d_cnt, 2 * (size_t)nsys));
+    CK(nullptr, dalloc(&c->d_mask, (size_t)nsys));
+    CK(nullptr, dalloc(&c->d_ksys, (size_t)nsys * nrhs));
+    CK(nullptr, dalloc(&c->d_kpar, (size_t)nsys * nrhs));
+    CK(nullptr, dalloc(&c->d_rel, (size_t)nsys * nrhs));
+    CK(nullptr, dalloc(&c->d_sys_status, (size_t)nsys));
+    CK(nullptr, dalloc(&c->d_ndone, 1));
+    CK(nullptr, dalloc(&c->d_pss, 2 * (size_t)std::max(npairs, 1) * nrhs));
+    CK(nullptr, dalloc(&c->d_pmx, 2 * (size_t)std::max(npairs, 1) * nrhs));
+    CK(nullptr, dalloc(&c->d_row_sys, (size_t)n));
+    CK(nullptr, dalloc(&c->d_sys_off, (size_t)nsys + 1));
+    auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+        return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    std::vector<int32_t> row_sys(n);
+    for (int s = 0; s < nsys; ++s)
+        for (long long r = off[s]; r < off[s + 1]; ++r) row_sys[r] = s;
+    CK(nullptr, up(c->d_rowptr, big.rowptr.data(), (n + 1) * 4));
+    CK(nullptr, up(c->d_col, big.col.data(), nnz_off * 4));
+    CK(nullptr, up(c->d_T64, big.T.data(), nnz_off * 8));
+    if (o.precision == JAC_MIXED && nnz_off) {
+        std::vector<float> t32(nnz_off);
+        for (int64_t q = 0; q < nnz_off; ++q) t32[q] = (float)big.T[q];
+        CK(nullptr, up(c->d_T32, t32.data(), nnz_off * 4));
+    }
+    CK(nullptr, up(c->d_d, big.d.data(), n * 8));
+    CK(nullptr, up(c->d_row0, tl.row0.data(), tl.row0.size() * 4));
+    CK(nullptr, up(c->d_nnz0, tl.nnz0.data(), tl.nnz0.size() * 4));
+    CK(nullptr, up(c->d_cta0, tl.cta0.data(), tl.cta0.size() * 4));
+    CK(nullptr, up(c->d_tile_sys, tl.tile_part.data(), tl.tile_part.size() * 4));
+    CK(nullptr, up(c->d_sys_pair0, sys_pair0.data(), sys_pair0.size() * 4));
+    CK(nullptr, up(c->d_cta_pair0, cta_pair0.data(), cta_pair0.size() * 4));
+    CK(nullptr, up(c->d_cta_sys0, cta_sys0.data(), cta_sys0.size() * 4));
+    CK(nullptr, up(c->d_row_sys, row_sys.data(), row_sys.size() * 4));
+    CK(nullptr, up(c->d_sys_off, off.data(), off.size() * 8));
+    // right-hand sides: packed n x nrhs, then c = b / a_ii and ||b_s,q||
+    cudaStream_t sm = stream_of(C);
+    if (b) {
+        for (int s = 0; s < nsys; ++s) {
+            const size_t cnt = (size_t)(off[s + 1] - off[s]) * nrhs;
+            if (!b[s]) {
+                CK(nullptr, cudaMemsetAsync(c->d_bstage + off[s] * nrhs, 0, cnt * 8, sm));
+                continue;
+            }
+            CK(nullptr, cudaMemcpyAsync(c->d_bstage + off[s] * nrhs, b[s], cnt * 8,
+                                        memory == JAC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                        sm));
+        }
+    }
+    CK(nullptr, launch_batched_c(c->d_bstage, c->d_d, c->d_c, n, nrhs, sm));
+    CK(nullptr, launch_batched_bnorm(c->d_bstage, c->d_sys_off, nsys, nrhs, c->d_bnorm, sm));
+    CK(nullptr, launch_batched_reset(devbatch(C), nrhs, sm));
+    CK(nullptr, launch_reset_iterate(c->d_ctl, sm));
+    CK(nullptr, launch_arm(c->d_ctl, 0, 0, o.inner_sweeps, 0, 0, -1.0, o.norm, nullptr, 0,
+                           (long long)o.timeout_cycles, -1, sm));
+    if (fetch_ctl(C, &c->h_ctl[0]) != JAC_OK) return fail(nullptr, JAC_ECUDA, C->err);
+    CK(nullptr, sm ? cudaStreamSynchronize(sm) : cudaDeviceSynchronize());
+    *out = c.release();
+    return JAC_OK;
 }
 
 jac_status jac_set_x(jac_ctx* c, const double* x, int32_t memory)
@@ -696,6 +978,22 @@ jac_status jac_set_x(jac_ctx* c, const double* x, int32_t memory)
     if (!c) return JAC_EINVAL;
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
+    if (c->batched) {
+        const size_t cnt = (size_t)c->n * c->nrhs;
+        if (x) {
+            if (memory != JAC_MEM_HOST && memory != JAC_MEM_DEVICE) return fail(c, JAC_EINVAL, "bad memory");
+            CK(c, cudaMemcpyAsync(c->d_x[0], x, cnt * 8,
+                                  memory == JAC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        } else {
+            CK(c, cudaMemsetAsync(c->d_x[0], 0, cnt * 8, s));
+        }
+        CK(c, launch_batched_reset(devbatch(c), c->nrhs, s));
+        CK(c, launch_reset_iterate(c->d_ctl, s));
+        if (fetch_ctl(c, &c->h_ctl[0]) != JAC_OK) return JAC_ECUDA;
+        CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
+        c->sweeps_total = 0;
+        return JAC_OK;
+    }
     if (x) {
         jac_status st = copy_to_stage(c, x, memory, (size_t)c->n, c->d_stage);
         if (st != JAC_OK) return st;
@@ -713,6 +1011,16 @@ jac_status jac_set_b(jac_ctx* c, const double* b, int32_t memory)
     if (!c) return JAC_EINVAL;
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
+    if (c->batched) {
+        const size_t cnt = (size_t)c->n * c->nrhs;
+        if (b) CK(c, cudaMemcpyAsync(c->d_bstage, b, cnt * 8,
+                                     memory == JAC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        else CK(c, cudaMemsetAsync(c->d_bstage, 0, cnt * 8, s));
+        CK(c, launch_batched_c(c->d_bstage, c->d_d, c->d_c, c->n, c->nrhs, s));
+        CK(c, launch_batched_bnorm(c->d_bstage, c->d_sys_off, c->nsys, c->nrhs, c->d_bnorm, s));
+        CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
+        return JAC_OK;
+    }
     if (b) {
         jac_status st = copy_to_stage(c, b, memory, (size_t)c->n, c->d_stage);
         if (st != JAC_OK) return st;
@@ -732,6 +1040,10 @@ jac_status jac_sweep(jac_ctx* c, int32_t k, double* relres_out)
     }
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
+    if (c->batched) {
+        jac_status st0 = batched_restart(c);
+        if (st0 != JAC_OK) return st0;
+    }
     jac_status st = arm(c, 0, 0, 0, k, -1.0);
     if (st != JAC_OK) return st;
     const int launches = (k + c->K - 1) / c->K;
@@ -763,6 +1075,10 @@ jac_status jac_solve(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out,
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
     const bool mixed = (c->precision == JAC_MIXED);
+    if (c->batched) {
+        jac_status st0 = batched_restart(c);
+        if (st0 != JAC_OK) return st0;
+    }
     jac_status st = arm(c, 1, mixed ? 1 : 0, maxit, -1, tol);
     if (st != JAC_OK) return st;
     CK(c, cudaEventRecord(c->ev0, s));
@@ -826,6 +1142,24 @@ jac_status jac_solve(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out,
     if (st != JAC_OK) return st;
     c->sweeps_total = h.k;
     c->outer_last = h.outer;
+    if (c->batched) {
+        // every system stopped on its own: converged, or at maxit
+        std::vector<int> sst(c->nsys);
+        std::vector<double> rel((size_t)c->nsys * c->nrhs);
+        CK(c, cudaMemcpy(sst.data(), c->d_sys_status, sst.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        CK(c, cudaMemcpy(rel.data(), c->d_rel, rel.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        double worst = 0.0;
+        for (double r : rel) worst = std::max(worst, r);
+        if (sweeps_out) *sweeps_out = h.k;
+        if (relres_out) *relres_out = worst;
+        bool limit = false;
+        for (int v : sst) {
+            if (v == DONE_NUMERIC) return fail(c, JAC_ENUMERIC, "a residual became NaN or Inf");
+            if (v != DONE_CONVERGED) limit = true;
+        }
+        if (limit) return fail(c, JAC_ENOTCONV, "maxit reached before the tolerance in some system");
+        return JAC_OK;
+    }
     if (sweeps_out) *sweeps_out = h.k;
     if (relres_out) *relres_out = h.relres;
     if (h.done == DONE_LIMIT) return fail(c, JAC_ENOTCONV, "maxit reached before the tolerance");
@@ -839,11 +1173,20 @@ jac_status jac_get_x(jac_ctx* c, double* x, int32_t memory)
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
     const int xb = c->h_ctl[0].xbuf & 1;
-    CK(c, launch_scatter_rows(c->d_perm, c->d_x[xb], c->d_stage, (int)c->n, 1, s));
+    double* src = c->d_stage;
+    size_t cnt = (size_t)c->n;
+    if (c->batched) {
+        src = c->d_bstage;
+        cnt = (size_t)c->n * c->nrhs;
+        CK(c, launch_batched_gather_x(c->d_x[0], c->d_x[1], c->d_row_sys, c->d_mask, c->d_kpar, xb, c->n, c->nrhs,
+                                      src, s));
+    } else {
+        CK(c, launch_scatter_rows(c->d_perm, c->d_x[xb], c->d_stage, (int)c->n, 1, s));
+    }
     if (memory == JAC_MEM_DEVICE) {
-        CK(c, cudaMemcpyAsync(x, c->d_stage, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CK(c, cudaMemcpyAsync(x, src, cnt * sizeof(double), cudaMemcpyDeviceToDevice, s));
     } else if (memory == JAC_MEM_HOST) {
-        CK(c, cudaMemcpyAsync(x, c->d_stage, c->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(c, cudaMemcpyAsync(x, src, cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
     } else {
         return fail(c, JAC_EINVAL, "memory must be JAC_MEM_HOST or JAC_MEM_DEVICE");
     }
@@ -867,8 +1210,19 @@ jac_status jac_get_history(jac_ctx* c, double* out, int64_t max, int64_t* count)
 jac_status jac_get_batch_results(jac_ctx* c, int64_t* sweeps, double* relres)
 {
     if (!c) return JAC_EINVAL;
-    if (sweeps) sweeps[0] = c->h_ctl[0].k;
-    if (relres) relres[0] = c->h_ctl[0].relres;
+    if (!c->batched) {
+        if (sweeps) sweeps[0] = c->h_ctl[0].k;
+        if (relres) relres[0] = c->h_ctl[0].relres;
+        return JAC_OK;
+    }
+    DeviceGuard g(c->device);
+    const size_t cnt = (size_t)c->nsys * c->nrhs;
+    if (sweeps) {
+        std::vector<long long> k(cnt);
+        CK(c, cudaMemcpy(k.data(), c->d_ksys, cnt * sizeof(long long), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < cnt; ++i) sweeps[i] = k[i];
+    }
+    if (relres) CK(c, cudaMemcpy(relres, c->d_rel, cnt * sizeof(double), cudaMemcpyDeviceToHost));
     return JAC_OK;
 }
 

@@ -1,0 +1,582 @@
+// Batched solves: many independent systems, each with NRHS right-hand sides,
+// in one persistent launch.
+//
+// The systems are packed as one block-diagonal matrix (rows of system s are
+// [off_s, off_{s+1})); row tiles never cross a system.  Every sweep is the
+// synchronous Jacobi sweep of Sec. 3 applied to all right-hand sides of every
+// active system at once, so each matrix entry read from HBM serves NRHS
+// updates.  Each system, and each of its right-hand sides, keeps its own
+// residual norm and stopping test (Algorithm 1): a right-hand side stops at
+// its first iterate whose test value is <= tol (that iterate is kept), and a
+// system whose right-hand sides have all stopped is skipped from then on.
+//
+// Norms: every CTA reduces the rows it owns of a system into a per-(CTA,
+// system) partial; the last CTA to finish a system in a sweep (an atomic
+// arrival count) reduces that system's partials in CTA order -- a fixed
+// order -- and takes the system's decisions, which the grid barrier at the
+// end of the sweep publishes.
+#include <cuda_runtime.h>
+
+#include "jac_device.cuh"
+#include "jac_launch.h"
+
+namespace jac {
+
+constexpr int BCHUNK = 3;    // entries per row whose NRHS-wide x gathers are issued together
+
+__device__ __forceinline__ void b_consumer_sync(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_b(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct BStageLayout {
+    int o_val, o_col, o_rp, o_c, o_d, bytes;
+};
+
+__host__ __device__ inline BStageLayout bstage_layout(int rows, int emax, int nrhs)
+{
+    auto up = [](int v) { return (v + 127) & ~127; };
+    BStageLayout L;
+    L.o_val = 128;
+    L.o_col = L.o_val + up((emax + 4) * 8);
+    L.o_rp = L.o_col + up((emax + 8) * 4);
+    L.o_c = L.o_rp + up((rows + 12) * 4);
+    L.o_d = L.o_c + up((rows + 4) * nrhs * 8);
+    L.bytes = L.o_d + up((rows + 4) * 8);
+    return L;
+}
+
+int batched_smem_bytes(int rows, int emax, int nrhs, int stages)
+{
+    return stages * bstage_layout(rows, emax, nrhs).bytes + 2 * stages * 8 + 64;
+}
+
+template <int NRHS>
+__device__ __forceinline__ void load_rhs(const double* p, double (&v)[NRHS])
+{
+    if constexpr (NRHS % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < NRHS; q += 2) {
+            const double2 t = __ldcg(reinterpret_cast<const double2*>(p) + q / 2);
+            v[q] = t.x;
+            v[q + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) v[q] = __ldcg(p + q);
+    }
+}
+
+template <int NRHS>
+__device__ __forceinline__ void load_rhs(const float* p, float (&v)[NRHS])
+{
+    if constexpr (NRHS == 4) {
+        const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (NRHS == 2) {
+        const float2 t = __ldcg(reinterpret_cast<const float2*>(p));
+        v[0] = t.x; v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) v[q] = __ldcg(p + q);
+    }
+}
+
+// acc[q] += sum_k T_k x[col_k][q] for the row's entries in stored order.
+template <int NRHS, class Real, class LdT, class LdC>
+__device__ __forceinline__ void brow_dot(Real (&acc)[NRHS], int kb, int len, const Real* __restrict__ xs, LdT ldt,
+                                         LdC ldc)
+{
+    int lmax = (int)__reduce_max_sync(__activemask(), (unsigned)len);
+    for (int o = 0; o < lmax; o += BCHUNK) {
+        Real xv[BCHUNK][NRHS];
+#pragma unroll
+        for (int u = 0; u < BCHUNK; ++u)
+            if (o + u < len) load_rhs<NRHS>(xs + (size_t)ldc(kb + o + u) * NRHS, xv[u]);
+#pragma unroll
+        for (int u = 0; u < BCHUNK; ++u) {
+            if (o + u >= lmax) break;
+            if (o + u < len) {
+                const Real t = ldt(kb + o + u);
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q) {
+                    if constexpr (sizeof(Real) == 8) acc[q] = __fma_rn(t, xv[u][q], acc[q]);
+                    else acc[q] = __fmaf_rn(t, xv[u][q], acc[q]);
+                }
+            }
+        }
+    }
+}
+
+template <int NRHS, int STAGES, bool MIXED, int NWM>
+__global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBatch bt, JacCtl* ctl, int max_sweeps)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int CT = NWM * 32, NW = NWM, ROWS = CT;
+    const BStageLayout L = bstage_layout(ROWS, t.emax, NRHS);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes);
+    uint64_t* empty = full + STAGES;
+    __shared__ double s_wss[NW][NRHS];
+    __shared__ unsigned long long s_wmx[NW][NRHS];
+    __shared__ long long s_k, s_klim, s_evals, s_outer, s_timeout;
+    __shared__ int s_xb, s_phase, s_inner, s_test, s_start, s_fail, s_stop_all, s_norm;
+    __shared__ double s_tol;
+    __shared__ volatile int s_stop;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        const volatile JacCtl* c = ctl;
+        s_k = c->k;
+        s_klim = c->k_limit;
+        s_evals = c->evals;
+        s_outer = c->outer;
+        s_timeout = c->timeout;
+        s_xb = c->xbuf;
+        s_phase = c->phase;
+        s_inner = c->inner < 2 ? 2 : c->inner;
+        s_test = c->test;
+        s_tol = c->tol;
+        s_norm = c->norm_kind;
+        s_start = (c->done == DONE_RUNNING) && (c->status == 0);
+        s_stop = 0;
+        s_fail = 0;
+        s_stop_all = 0;
+        for (int q = 0; q < STAGES; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], NW);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (!s_start) return;
+
+    const int tb = t.cta0[blockIdx.x], te = t.cta0[blockIdx.x + 1], nt = te - tb;
+    int ksw = max_sweeps;
+    if (!MIXED && !s_test) {
+        const long long rem = s_klim - s_k;
+        ksw = (int)(rem < (long long)ksw ? (rem > 0 ? rem : 0) : ksw);
+    }
+    const long long njobs = (long long)ksw * nt;
+    const int inner = s_inner, phase0 = s_phase, emax = t.emax;
+    const long long budget = s_timeout;
+    constexpr int ALL = (1 << NRHS) - 1;
+
+    // ================================================= producer warp
+    if (warp == NW) {
+        if (lane == 0) {
+            const uint64_t pol = policy_evict_first();
+            int cached_sys = -1, cached_mask = 0;
+            long long issued = 0;
+            for (long long j = 0; j < njobs; ++j) {
+                const int sidx = (int)(j % STAGES);
+                if (j >= STAGES) {
+                    const unsigned par = (unsigned)(((j / STAGES) - 1) & 1);
+                    bool ok = mbar_try_wait(&empty[sidx], par);
+                    if (!ok) {
+                        const long long t0 = clock64();
+                        while (!(ok = mbar_try_wait(&empty[sidx], par))) {
+                            if (s_stop) break;
+                            if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); break; }
+                        }
+                    }
+                    if (!ok) break;
+                }
+                const int sw = (int)(j / nt);
+                const int ti = tb + (int)(j - (long long)sw * nt);
+                const int sys = __ldg(bt.tile_sys + ti);
+                if (sys != cached_sys || (j % nt) == 0) {   // refresh at system changes and sweep starts
+                    cached_sys = sys;
+                    cached_mask = ld_volatile_i32(bt.mask + sys);
+                }
+                uint64_t* bar = &full[sidx];
+                if (cached_mask == ALL) {        // retired system: an empty job
+                    mbar_expect_tx(bar, 0);
+                    issued = j + 1;
+                    continue;
+                }
+                const int ph = phase_of(MIXED, MIXED ? (phase0 + sw) % inner : 0, inner);
+                const bool fp64 = (ph == PH_P64 || ph == PH_P64R);
+                unsigned char* st = smem + sidx * L.bytes;
+                const int r0 = __ldg(t.row0 + ti), r1 = __ldg(t.row0 + ti + 1);
+                const int p0 = __ldg(t.nnz0 + ti), p1 = __ldg(t.nnz0 + ti + 1);
+                const bool over = (p1 - p0) > emax;
+                unsigned bytes = 0;
+                int vb = 0, ve = 0, cb = 0, ce = 0;
+                if (!over) {
+                    if (fp64) { vb = p0 & ~1; ve = (p1 + 1) & ~1; bytes += (unsigned)(ve - vb) * 8u; }
+                    else { vb = p0 & ~3; ve = (p1 + 3) & ~3; bytes += (unsigned)(ve - vb) * 4u; }
+                    cb = p0 & ~3; ce = (p1 + 3) & ~3;
+                    bytes += (unsigned)(ce - cb) * 4u;
+                }
+                const int rb = r0 & ~3, re = (r1 + 1 + 3) & ~3;
+                bytes += (unsigned)(re - rb) * 4u;
+                const int hb = r0 & ~1, he = (r1 + 1) & ~1;
+                if (fp64) bytes += (unsigned)(he - hb) * 8u * (NRHS + 1);
+                mbar_expect_tx(bar, bytes);
+                if (!over) {
+                    if (ve > vb) {
+                        if (fp64) bulk_g2s(st + L.o_val, m.T64 + vb, (unsigned)(ve - vb) * 8u, bar, pol);
+                        else bulk_g2s(st + L.o_val, m.T32 + vb, (unsigned)(ve - vb) * 4u, bar, pol);
+                    }
+                    if (ce > cb) bulk_g2s(st + L.o_col, m.col + cb, (unsigned)(ce - cb) * 4u, bar, pol);
+                }
+                bulk_g2s(st + L.o_rp, m.rowptr + rb, (unsigned)(re - rb) * 4u, bar, pol);
+                if (fp64 && he > hb) {
+                    bulk_g2s(st + L.o_c, m.c + (size_t)hb * NRHS, (unsigned)(he - hb) * 8u * NRHS, bar, pol);
+                    bulk_g2s(st + L.o_d, m.d + hb, (unsigned)(he - hb) * 8u, bar, pol);
+                }
+                issued = j + 1;
+            }
+            const long long t0 = clock64();
+            for (long long j = (issued > STAGES ? issued - STAGES : 0); j < issued; ++j) {
+                const unsigned par = (unsigned)((j / STAGES) & 1);
+                while (!mbar_try_wait(&full[(int)(j % STAGES)], par))
+                    if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); break; }
+            }
+        }
+        return;
+    }
+
+    // ================================================= math warps
+    long long k = s_k;
+    int xb = s_xb, pos = phase0;
+    long long evals = s_evals, outer = s_outer;
+    long long jc = 0;
+    int nbar = 0;
+    const int my_pair0 = bt.cta_pair0[blockIdx.x], my_sys0 = bt.cta_sys0[blockIdx.x];
+    for (int sw = 0; sw < ksw; ++sw) {
+        const int ph = phase_of(MIXED, pos, inner);
+        const bool norm_ph = (ph == PH_P64 || ph == PH_P64R);
+        const double* xs = v.x[xb];
+        double* xd = v.x[xb ^ 1];
+        const float* es = v.e[pos & 1];
+        float* ed = v.e[(pos + 1) & 1];
+        double ss[NRHS];
+        unsigned long long mx[NRHS];
+        int cur = -1, msk = ALL;
+        // per-(CTA, system) partials: block reduction, then the last CTA of the system decides
+        auto finish = [&](int sys) {
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) {
+                const double a = warp_sum(ss[q]);
+                const unsigned long long b2 = warp_max(mx[q]);
+                if (lane == 0) { s_wss[warp][q] = a; s_wmx[warp][q] = b2; }
+            }
+            b_consumer_sync(CT);
+            if (tid == 0) {
+                const int slot = my_pair0 + (sys - my_sys0);
+                const int par = sw & 1;
+                for (int q = 0; q < NRHS; ++q) {
+                    double a = 0.0;
+                    unsigned long long b2 = 0;
+                    for (int w = 0; w < NW; ++w) { a += s_wss[w][q]; b2 = umax64(b2, s_wmx[w][q]); }
+                    __stcg(bt.pss + ((size_t)par * bt.npairs + slot) * NRHS + q, a);
+                    __stcg(bt.pmx + ((size_t)par * bt.npairs + slot) * NRHS + q, b2);
+                }
+                __threadfence();
+                const unsigned arrived = atomicAdd(bt.cnt + par * bt.nsys + sys, 1u);
+                if (arrived == (unsigned)(__ldg(bt.sys_pair0 + sys + 1) - __ldg(bt.sys_pair0 + sys)) - 1) {
+                    __threadfence();
+                    bt.cnt[par * bt.nsys + sys] = 0;
+                    const int pb = __ldg(bt.sys_pair0 + sys), pe = __ldg(bt.sys_pair0 + sys + 1);
+                    int mk = ld_volatile_i32(bt.mask + sys);
+                    for (int q = 0; q < NRHS; ++q) {
+                        if (mk & (1 << q)) continue;
+                        double a = 0.0;
+                        unsigned long long b2 = 0;
+                        for (int pp = pb; pp < pe; ++pp) {
+                            a += __ldcg(bt.pss + ((size_t)par * bt.npairs + pp) * NRHS + q);
+                            b2 = umax64(b2, __ldcg(bt.pmx + ((size_t)par * bt.npairs + pp) * NRHS + q));
+                        }
+                        const double bn = bt.bnorm[sys * NRHS + q];
+                        const Decision d = decide(s_test, s_tol, s_klim, s_norm, bn, a, b2, k);
+                        bt.rel[sys * NRHS + q] = d.relres;
+                        bt.ksys[sys * NRHS + q] = k;
+                        bt.kpar[sys * NRHS + q] = xb;
+                        if (d.done != DONE_RUNNING) {
+                            mk |= 1 << q;
+                            if (d.done == DONE_NUMERIC) atomicOr(&ctl->status, ST_NUMERIC);
+                            if (d.done == DONE_LIMIT) bt.sys_status[sys] = DONE_LIMIT;
+                            if (d.done == DONE_NUMERIC) bt.sys_status[sys] = DONE_NUMERIC;
+                        }
+                    }
+                    if (mk != ld_volatile_i32(bt.mask + sys)) {
+                        bt.mask[sys] = mk;
+                        if (mk == ALL) {
+                            if (bt.sys_status[sys] == DONE_RUNNING) bt.sys_status[sys] = DONE_CONVERGED;
+                            atomicAdd(bt.ndone, 1u);
+                        }
+                    }
+                    __threadfence();
+                }
+            }
+            b_consumer_sync(CT);
+        };
+        for (int i = 0; i < nt; ++i, ++jc) {
+            const int ti = tb + i;
+            const int sys = __ldg(bt.tile_sys + ti);
+            if (sys != cur) {
+                if (cur >= 0 && msk != ALL && norm_ph) finish(cur);
+                cur = sys;
+                msk = ld_volatile_i32(bt.mask + sys);
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q) { ss[q] = 0.0; mx[q] = 0; }
+            }
+            const int sidx = (int)(jc % STAGES);
+            uint64_t* bar = &full[sidx];
+            const unsigned par = (unsigned)((jc / STAGES) & 1);
+            bool ok = mbar_try_wait(bar, par);
+            if (!ok && !s_fail) {
+                const long long t0 = clock64();
+                while (!(ok = mbar_try_wait(bar, par))) {
+                    if (s_fail) break;
+                    if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); s_fail = 1; break; }
+                }
+            }
+            if (ok && msk != ALL) {
+                const unsigned char* st = smem + sidx * L.bytes;
+                const int r0 = __ldg(t.row0 + ti), r1 = __ldg(t.row0 + ti + 1);
+                const int p0 = __ldg(t.nnz0 + ti), p1 = __ldg(t.nnz0 + ti + 1);
+                const bool over = (p1 - p0) > emax;
+                const int* srp = reinterpret_cast<const int*>(st + L.o_rp) - (r0 & ~3);
+                const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (p0 & ~3);
+                const int r = r0 + tid;
+                const bool in = r < r1;
+                const int kb = in ? srp[r] : 0, len = in ? srp[r + 1] - kb : 0;
+                if (norm_ph) {
+                    const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
+                    const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (size_t)(r0 & ~1) * NRHS;
+                    const double* sd = reinterpret_cast<const double*>(st + L.o_d) - (r0 & ~1);
+                    double acc[NRHS], xi[NRHS];
+#pragma unroll
+                    for (int q = 0; q < NRHS; ++q) { acc[q] = in ? sc[(size_t)r * NRHS + q] : 0.0; xi[q] = 0.0; }
+                    if (in) load_rhs<NRHS>(xs + (size_t)r * NRHS, xi);
+                    if (!over)
+                        brow_dot<NRHS>(acc, kb, len, xs, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; });
+                    else
+                        brow_dot<NRHS>(acc, kb, len, xs, [&](int e) { return __ldg(m.T64 + e); },
+                                       [&](int e) { return __ldg(m.col + e); });
+                    if (in) {
+                        const double di = sd[r];
+#pragma unroll
+                        for (int q = 0; q < NRHS; ++q) {
+                            if (msk & (1 << q)) continue;        // stopped: its iterate stays where it is
+                            if (ph == PH_P64) {
+                                __stcg(xd + (size_t)r * NRHS + q, acc[q]);
+                            } else {
+                                const float dl = (float)__dadd_rn(acc[q], -xi[q]);
+                                __stcg(v.dlt + (size_t)r * NRHS + q, dl);
+                                __stcg(v.e[1] + (size_t)r * NRHS + q, dl);
+                            }
+                            accumulate_residual(acc[q], xi[q], di, ss[q], mx[q]);
+                        }
+                    }
+                } else {
+                    const float* sv = reinterpret_cast<const float*>(st + L.o_val) - (p0 & ~3);
+                    float acc[NRHS];
+#pragma unroll
+                    for (int q = 0; q < NRHS; ++q) acc[q] = 0.f;
+                    if (in) load_rhs<NRHS>(v.dlt + (size_t)r * NRHS, acc);
+                    if (!over)
+                        brow_dot<NRHS>(acc, kb, len, es, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; });
+                    else
+                        brow_dot<NRHS>(acc, kb, len, es, [&](int e) { return __ldg(m.T32 + e); },
+                                       [&](int e) { return __ldg(m.col + e); });
+                    if (in) {
+#pragma unroll
+                        for (int q = 0; q < NRHS; ++q) {
+                            if (ph == PH_P32) {
+                                __stcg(ed + (size_t)r * NRHS + q, acc[q]);
+                            } else if (!(msk & (1 << q))) {
+                                double* px = v.x[xb] + (size_t)r * NRHS + q;
+                                __stcg(px, __dadd_rn(__ldcg(px), (double)acc[q]));
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive_b(&empty[sidx]);
+        }
+        if (cur >= 0 && msk != ALL && norm_ph) finish(cur);
+        // ---- grid barrier
+        b_consumer_sync(CT);
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(&ctl->bar, 1ull);
+            const unsigned long long target = (unsigned long long)(nbar + 1) * gridDim.x;
+            const long long t0 = clock64();
+            while (ld_acquire_u64(&ctl->bar) < target) {
+                if (ld_volatile_i32(&ctl->status) & ST_TIMEOUT) { s_fail = 1; break; }
+                if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); s_fail = 1; break; }
+                __nanosleep(32);
+            }
+            __threadfence();
+            s_stop_all = (int)(*(volatile unsigned*)bt.ndone >= (unsigned)bt.nsys);
+        }
+        ++nbar;
+        b_consumer_sync(CT);
+        if (s_fail) break;
+        if (norm_ph) {
+            evals += 1;
+            if (s_test && s_stop_all) break;
+            if (ph == PH_P64) { k += 1; xb ^= 1; }
+            else pos = 1;
+        } else if (ph == PH_P32) {
+            pos += 1;
+        } else {
+            pos = 0;
+            k += inner;
+            outer += 1;
+        }
+        if (!MIXED && !s_test && k >= s_klim) break;
+    }
+    if (tid == 0) s_stop = 1;
+    if (blockIdx.x == 0 && tid == 0) {
+        ctl->k = k;
+        ctl->xbuf = xb;
+        ctl->phase = pos;
+        ctl->evals = evals;
+        ctl->outer = outer;
+        ctl->done = (s_test && s_stop_all) ? DONE_CONVERGED : DONE_RUNNING;
+        __threadfence();
+    }
+}
+
+template <int NRHS, bool MIXED>
+static const void* batched_fn()
+{
+    return reinterpret_cast<const void*>(&k_batched<NRHS, 4, MIXED, 7>);
+}
+
+const void* batched_kernel(int nrhs, bool mixed)
+{
+    switch (nrhs) {
+    case 1: return mixed ? batched_fn<1, true>() : batched_fn<1, false>();
+    case 2: return mixed ? batched_fn<2, true>() : batched_fn<2, false>();
+    case 4: return mixed ? batched_fn<4, true>() : batched_fn<4, false>();
+    default: return nullptr;
+    }
+}
+
+int batched_threads() { return 7 * 32 + 32; }
+int batched_rows() { return 7 * 32; }
+
+cudaError_t launch_batched(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
+                           const DevTiles& t, const DevBatch& bt, JacCtl* ctl, int max_sweeps, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {(void*)&m, (void*)&v, (void*)&t, (void*)&bt, (void*)&ctl, (void*)&max_sweeps};
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+// ----------------------------------------------------------- helpers
+
+// c[r][q] = b_perm(r)[q] / a_rr for the packed systems (identity permutation).
+__global__ void k_batched_c(const double* __restrict__ b, const double* __restrict__ d, double* __restrict__ c,
+                            long long n, int nrhs)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nrhs) return;
+    c[i] = __ddiv_rn(b[i], d[i / nrhs]);
+}
+
+// ||b_s,q||_2 for every system (one CTA per system, fixed order).
+__global__ void __launch_bounds__(256) k_batched_bnorm(const double* __restrict__ b, const long long* __restrict__ off,
+                                                       int nrhs, double* __restrict__ bnorm)
+{
+    __shared__ double sh[8];
+    const int s = blockIdx.x;
+    const long long r0 = off[s], r1 = off[s + 1];
+    for (int q = 0; q < nrhs; ++q) {
+        double a = 0.0;
+        for (long long r = r0 + threadIdx.x; r < r1; r += 256) a = __fma_rn(b[r * nrhs + q], b[r * nrhs + q], a);
+        a = warp_sum(a);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += sh[w];
+            bnorm[s * nrhs + q] = sqrt(t);
+        }
+        __syncthreads();
+    }
+}
+
+// x_out[r][q] = x[kpar(s,q)][r][q]: each right-hand side from the buffer that holds its final iterate.
+__global__ void k_batched_gather_x(const double* __restrict__ x0, const double* __restrict__ x1,
+                                   const int* __restrict__ row_sys, const int* __restrict__ mask,
+                                   const int* __restrict__ kpar, int cur, long long n, int nrhs, double* __restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nrhs) return;
+    const long long r = i / nrhs;
+    const int q = (int)(i - r * nrhs);
+    const int s = row_sys[r];
+    const int p = (mask[s] >> q) & 1 ? kpar[s * nrhs + q] : cur;
+    out[i] = (p & 1) ? x1[i] : x0[i];
+}
+
+__global__ void k_batched_reset(int* mask, long long* ksys, double* rel, int* kpar, int* sys_status, unsigned* cnt,
+                                unsigned* ndone, int nsys, int nrhs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nsys) {
+        mask[i] = 0;
+        sys_status[i] = DONE_RUNNING;
+        cnt[i] = 0;
+        cnt[nsys + i] = 0;
+    }
+    if (i < nsys * nrhs) {
+        ksys[i] = -1;
+        rel[i] = 0.0;
+        kpar[i] = 0;
+    }
+    if (i == 0) *ndone = 0;
+}
+
+cudaError_t launch_batched_c(const double* b, const double* d, double* c, long long n, int nrhs, cudaStream_t s)
+{
+    const long long tot = n * nrhs;
+    k_batched_c<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(b, d, c, n, nrhs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_bnorm(const double* b, const long long* off, int nsys, int nrhs, double* bnorm,
+                                 cudaStream_t s)
+{
+    k_batched_bnorm<<<nsys, 256, 0, s>>>(b, off, nrhs, bnorm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_gather_x(const double* x0, const double* x1, const int* row_sys, const int* mask,
+                                    const int* kpar, int cur, long long n, int nrhs, double* out, cudaStream_t s)
+{
+    const long long tot = n * nrhs;
+    k_batched_gather_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x0, x1, row_sys, mask, kpar, cur, n, nrhs, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_reset(const DevBatch& bt, int nrhs, cudaStream_t s)
+{
+    const int tot = bt.nsys * nrhs;
+    k_batched_reset<<<(tot + 255) / 256, 256, 0, s>>>(bt.mask, bt.ksys, bt.rel, bt.kpar, bt.sys_status, bt.cnt,
+                                                      bt.ndone, bt.nsys, nrhs);
+    return cudaGetLastError();
+}
+
+}  // namespace jac

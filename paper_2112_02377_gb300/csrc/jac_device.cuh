@@ -83,6 +83,25 @@ struct DevTiles {
     int blkcap;               // halo kernel: run-block capacity per CTA (int4)
 };
 
+// Per-system state of a batched context (systems packed block-diagonally).
+struct DevBatch {
+    int nsys, npairs;
+    const int* tile_sys;        // ntiles: system of each tile
+    const int* sys_pair0;       // nsys+1: each system's (CTA, system) partial slots, contiguous
+    const int* cta_pair0;       // ctas: first partial slot of each CTA
+    const int* cta_sys0;        // ctas: first system of each CTA
+    const double* bnorm;        // nsys*nrhs: ||b_s,q||_2
+    unsigned* cnt;              // [2][nsys] arrivals of CTAs that finished a system in a sweep
+    int* mask;                  // nsys: bit q set = right-hand side q has stopped
+    long long* ksys;            // nsys*nrhs: iterate of the last evaluation (the stopping one once stopped)
+    int* kpar;                  // nsys*nrhs: x buffer that holds that iterate (FP64 ping-pong)
+    double* rel;                // nsys*nrhs: test value of that iterate
+    int* sys_status;            // nsys: DONE_*
+    unsigned* ndone;            // systems whose right-hand sides have all stopped
+    double* pss;                // [2][npairs][nrhs] partial sum of r^2
+    unsigned long long* pmx;    // [2][npairs][nrhs] partial max |r| (bits)
+};
+
 __device__ __forceinline__ unsigned long long abs_bits(double r)
 {
     return (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
@@ -105,6 +124,26 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v)
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_down_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Residual bookkeeping of one row from its update: r = a_ii (x' - x).
+__device__ __forceinline__ void accumulate_residual(double xnew, double xold, double di, double& ss,
+                                                    unsigned long long& mx)
+{
+    const double dl = __dadd_rn(xnew, -xold);
+    const double r = __dmul_rn(di, dl);
+    ss = __fma_rn(r, r, ss);
+    mx = umax64(mx, abs_bits(r));
+}
+
+// Phase of a sweep: plain FP64 sweeps, or position `pos` in the mixed
+// refinement cycle of `inner` sweeps (FP64 residual pass, FP32 inner sweeps,
+// last inner sweep fused with x += e).
+__device__ __forceinline__ int phase_of(bool mixed, int pos, int inner)
+{
+    if (!mixed) return PH_P64;
+    if (pos == 0) return PH_P64R;
+    return pos == inner - 1 ? PH_P32L : PH_P32;
 }
 
 // Fixed-order reduction of `cnt` partials by one warp (lane 0 gets the result).

@@ -27,15 +27,6 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Residual bookkeeping of one row from its update.
-__device__ __forceinline__ void accumulate_residual(double xnew, double xold, double di, double& ss,
-                                                    unsigned long long& mx)
-{
-    const double dl = __dadd_rn(xnew, -xold);
-    const double r = __dmul_rn(di, dl);
-    ss = __fma_rn(r, r, ss);
-    mx = umax64(mx, abs_bits(r));
-}
 
 // RPT rows of one thread: acc[q] = acc[q] + sum_k T_k x_col(k), entries of each
 // row in stored order.  ldx(k) loads x_col(k) (an L2 gather or a read of the
@@ -262,12 +253,6 @@ int persistent_smem_bytes(int rows, int emax, int stages)
     return stages * stage_layout(rows, emax).bytes + 2 * stages * 8 + 64;
 }
 
-__device__ __forceinline__ int phase_of(bool mixed, int pos, int inner)
-{
-    if (!mixed) return PH_P64;
-    if (pos == 0) return PH_P64R;
-    return pos == inner - 1 ? PH_P32L : PH_P32;
-}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {

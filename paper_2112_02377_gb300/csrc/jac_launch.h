@@ -30,6 +30,18 @@ cudaError_t launch_arm(JacCtl* ctl, int test, int mixed, int inner, long long k_
                        cudaStream_t s);
 cudaError_t launch_reset_iterate(JacCtl* ctl, cudaStream_t s);
 cudaError_t launch_reset_bar(JacCtl* ctl, cudaStream_t s);
+const void* batched_kernel(int nrhs, bool mixed);
+int batched_smem_bytes(int rows, int emax, int nrhs, int stages);
+int batched_threads();
+int batched_rows();
+cudaError_t launch_batched(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
+                           const DevTiles& t, const DevBatch& bt, JacCtl* ctl, int max_sweeps, cudaStream_t s);
+cudaError_t launch_batched_c(const double* b, const double* d, double* c, long long n, int nrhs, cudaStream_t s);
+cudaError_t launch_batched_bnorm(const double* b, const long long* off, int nsys, int nrhs, double* bnorm,
+                                 cudaStream_t s);
+cudaError_t launch_batched_gather_x(const double* x0, const double* x1, const int* row_sys, const int* mask,
+                                    const int* kpar, int cur, long long n, int nrhs, double* out, cudaStream_t s);
+cudaError_t launch_batched_reset(const DevBatch& bt, int nrhs, cudaStream_t s);
 cudaError_t launch_adjoint_grad(const int* rowptr, const int* col, const double* lam, const double* x,
                                 double* dA, int n, cudaStream_t s);
 

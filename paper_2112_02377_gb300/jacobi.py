@@ -210,6 +210,27 @@ def jac_setup(A, b=None, splitting: int = JAC_BANDROW, nparts: int = 1, o: Optio
     return ctx
 
 
+def jac_setup_batched(As, bs, o: Optional[jac_opts] = None) -> ctypes.c_void_p:
+    """nsys systems solved together; bs[s] is n_s x nrhs (row-major) or None."""
+    nsys = len(As)
+    arr = (jac_csr * nsys)()
+    bp = (ctypes.c_void_p * nsys)()
+    keep = []
+    for i, A in enumerate(As):
+        s, k = make_csr(A.rowptr, A.col, A.val, A.n)
+        arr[i] = s
+        keep.append(k)
+    for i, b in enumerate(bs):
+        p, m, k = _buf(b, np.float64, "b")
+        bp[i] = p
+        keep.append(k)
+    o = o if o is not None else opts()
+    ctx = ctypes.c_void_p()
+    st = lib().jac_setup_batched(nsys, arr, bp, ctypes.byref(o), ctypes.byref(ctx))
+    _check(st, None)
+    return ctx
+
+
 def jac_set_x(ctx, x=None):
     p, m, keep = _buf(x, np.float64, "x")
     _check(lib().jac_set_x(ctx, p, m), ctx)
@@ -239,7 +260,10 @@ def jac_solve(ctx, tol: float, maxit: int, raise_on_notconv: bool = False) -> Tu
 def jac_get_x(ctx, out=None, n: Optional[int] = None):
     """Copy x^k into `out` (numpy or torch, host or device) or a new numpy array."""
     if out is None:
-        out = np.empty(n if n is not None else jac_stats(ctx)["n"])
+        if n is None:
+            st = jac_stats(ctx)
+            n = st["n"] * max(1, st["nrhs"])
+        out = np.empty(n)
     p, m, keep = _buf(out, np.float64, "out", writable=True)
     _check(lib().jac_get_x(ctx, p, m), ctx)
     return out
