@@ -103,6 +103,9 @@ typedef struct {
     int32_t tile_rows;         /* rows per tile: 0 = auto (256 FP64, 480 mixed), 224, 256 or 480
                                   (variant 2); 256 (variant 3) */
     int32_t ctas_per_sm;       /* variant 2 with 256-row tiles: 0 = auto (2), or 3 (3-stage pipeline) */
+    int32_t autotune;          /* 1: jac_setup / jac_setup_batched time a few sweeps of every kernel
+                                  geometry (variant, tile_rows, ctas_per_sm) and keep the fastest;
+                                  needs variant = tile_rows = ctas_per_sm = 0 */
     int32_t history;           /* >0: record the relres of every evaluated iterate,
                                   up to this many entries (jac_get_history) */
     void* stream;              /* cudaStream_t for all work; NULL = legacy default stream */
@@ -132,6 +135,7 @@ typedef struct {
     double bytes_per_sweep_fp64;  /* algorithmic HBM bytes of one FP64 sweep */
     double bytes_per_sweep_fp32;  /* algorithmic HBM bytes of one FP32 inner sweep */
     int32_t variant, precision, splitting, nrhs;
+    int32_t tile_rows, ctas_per_sm;  /* kernel geometry in use (chosen by the autotuner if enabled) */
 } jac_stats_t;
 
 /* Defaults for every option. */

@@ -65,6 +65,7 @@ struct jac_ctx {
     int* d_lcol = nullptr;
     int xcap = 0, maxruns = 0, ntcap = 0, blkcap = 0;
     int64_t fallback_tiles = 0, window_elems = 0;
+    int sms = 1;
     int ntiles = 0, emax = 0, rows_per_tile = 256, stages = 4, grid = 0, threads = 0, smem = 0;
     const void* pfn64 = nullptr;
     const void* pfnmix = nullptr;
@@ -434,6 +435,34 @@ jac_status check_opts(const jac_opts& o, jac_ctx* err_ctx)
     return JAC_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+
+// Device time per sweep of a freshly set-up context: a warm-up, then a timed
+// call (FP64: fixed sweeps; mixed: two refinement cycles of a solve that
+// cannot converge).  The iterate is reset to x^0 = 0 afterwards.
+double time_per_sweep(jac_ctx* c)
+{
+    double ms = 1e30;
+    if (c->precision == JAC_MIXED && !c->batched) {
+        int64_t k = 0;
+        double rel = 0.0;
+        const int64_t cyc = 2 * (int64_t)c->o.inner_sweeps;
+        jac_solve(c, 0.0, cyc - 1, &k, &rel);
+        jac_set_x(c, nullptr, JAC_MEM_HOST);
+        const jac_status st = jac_solve(c, 0.0, cyc - 1, &k, &rel);
+        if ((st == JAC_OK || st == JAC_ENOTCONV) && k > 0) ms = c->last_ms / (double)k;
+    } else {
+        double rel = 0.0;
+        if (jac_sweep(c, 8, &rel) == JAC_OK && jac_sweep(c, 24, &rel) == JAC_OK) ms = c->last_ms / 24.0;
+    }
+    jac_set_x(c, nullptr, JAC_MEM_HOST);
+    return ms;
+}
+
+struct Geometry {
+    int variant, rows, ctas;
+};
+
 }  // namespace
 
 // =========================================================================
@@ -519,6 +548,41 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     jac_opts o;
     jac_opts_default(&o);
     if (o_in) o = *o_in;
+    if (o.autotune) {
+        // Autotuner: set up every kernel geometry, time a few sweeps of each
+        // on this matrix, keep the fastest context.
+        if (o.variant || o.tile_rows || o.ctas_per_sm)
+            return fail(nullptr, JAC_EINVAL, "autotune needs variant = tile_rows = ctas_per_sm = 0");
+        const Geometry cand[] = {{2, 256, 2}, {2, 256, 3}, {2, 224, 0}, {2, 480, 0}, {3, 256, 0}};
+        jac_ctx* best = nullptr;
+        double best_ms = 1e30;
+        std::string first_err;
+        for (const Geometry& g : cand) {
+            jac_opts o2 = o;
+            o2.autotune = 0;
+            o2.variant = g.variant;
+            o2.tile_rows = g.rows;
+            o2.ctas_per_sm = g.ctas;
+            jac_ctx* c = nullptr;
+            const jac_status st = jac_setup(A, b, s, nparts, &o2, &c);
+            if (st != JAC_OK) {
+                if (first_err.empty()) first_err = g_setup_error;
+                if (st != JAC_EINVAL) return st;   // invalid matrix etc.: no geometry will do
+                continue;
+            }
+            const double ms = time_per_sweep(c);
+            if (ms < best_ms) {
+                if (best) jac_free(best);
+                best = c;
+                best_ms = ms;
+            } else {
+                jac_free(c);
+            }
+        }
+        if (!best) return fail(nullptr, JAC_EINVAL, "autotune: no kernel geometry could be set up: " + first_err);
+        *out = best;
+        return JAC_OK;
+    }
     if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
     jac_status st = check_opts(o, nullptr);
     if (st != JAC_OK) return st;
@@ -659,6 +723,7 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
             c->variant = 1;
         } else {
             c->grid = per_sm * prop.multiProcessorCount;
+            c->sms = prop.multiProcessorCount;
         }
     }
     if (c->variant == 1) {
@@ -760,12 +825,40 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     jac_opts o;
     jac_opts_default(&o);
     if (o_in) o = *o_in;
+    if (o.autotune) {
+        if (o.tile_rows) return fail(nullptr, JAC_EINVAL, "autotune needs tile_rows = 0");
+        jac_ctx* best = nullptr;
+        double best_ms = 1e30;
+        for (int rows : {224, 96}) {
+            jac_opts o2 = o;
+            o2.autotune = 0;
+            o2.tile_rows = rows;
+            jac_ctx* c = nullptr;
+            const jac_status st = jac_setup_batched(nsys, A, b, &o2, &c);
+            if (st != JAC_OK) {
+                if (st != JAC_EINVAL) return st;
+                continue;
+            }
+            const double ms = time_per_sweep(c);
+            if (ms < best_ms) {
+                if (best) jac_free(best);
+                best = c;
+                best_ms = ms;
+            } else {
+                jac_free(c);
+            }
+        }
+        if (!best) return fail(nullptr, JAC_EINVAL, "autotune: no batched geometry could be set up");
+        *out = best;
+        return JAC_OK;
+    }
     if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
     const int nrhs = o.nrhs;
     if (nrhs != 1 && nrhs != 2 && nrhs != 4) return fail(nullptr, JAC_EINVAL, "batched: opts.nrhs must be 1, 2 or 4");
     {
         jac_opts chk = o;
         chk.nrhs = 1;
+        chk.tile_rows = 0;
         jac_status st = check_opts(chk, nullptr);
         if (st != JAC_OK) return st;
     }
@@ -834,7 +927,8 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     // ---- launch configuration: 7 math warps + producer, 2 CTAs/SM, 4 stages
     cudaDeviceProp prop;
     CK(nullptr, cudaGetDeviceProperties(&prop, dev));
-    const int rows = batched_rows();
+    const int rows = o.tile_rows ? o.tile_rows : 224;
+    if (rows != 224 && rows != 96) return fail(nullptr, JAC_EINVAL, "batched: opts.tile_rows must be 0, 96 or 224");
     c->rows_per_tile = rows;
     c->stages = 4;
     {
@@ -842,10 +936,10 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
         const int64_t budget = 27 * 1024 - (int64_t)rows * (4 + 8 * nrhs + 8) - 1024;
         c->emax = (int)std::min<int64_t>(cap_entries, std::max<int64_t>(rows, budget / 12));
     }
-    c->pfn64 = batched_kernel(nrhs, false);
-    c->pfnmix = batched_kernel(nrhs, true);
+    c->pfn64 = batched_kernel(nrhs, false, rows);
+    c->pfnmix = batched_kernel(nrhs, true, rows);
     c->smem = batched_smem_bytes(rows, c->emax, nrhs, c->stages);
-    c->threads = batched_threads();
+    c->threads = batched_threads(rows);
     int per_sm = 0;
     {
         CK(nullptr, cudaFuncSetAttribute(c->pfn64, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
@@ -853,10 +947,11 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
         int a1 = 0, a2 = 0;
         CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a1, c->pfn64, c->threads, c->smem));
         CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, c->pfnmix, c->threads, c->smem));
-        per_sm = std::min(std::min(a1, a2), 2);
+        per_sm = std::min(std::min(a1, a2), rows == 96 ? 4 : 2);
     }
     if (per_sm < 1) return fail(nullptr, JAC_EINVAL, "batched kernel cannot be made co-resident");
     c->grid = per_sm * prop.multiProcessorCount;
+    c->sms = prop.multiProcessorCount;
     Tiling tl;
     make_tiling(big, plan, rows, c->emax, c->grid, tl);
     c->ntiles = (int)tl.ntiles();
@@ -1289,6 +1384,8 @@ jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
     out->precision = c->precision;
     out->splitting = c->splitting;
     out->nrhs = c->nrhs;
+    out->tile_rows = c->variant >= 2 ? c->rows_per_tile : 0;
+    out->ctas_per_sm = (c->variant >= 2 && c->n > 0 && c->grid > 0) ? c->grid / std::max(1, c->sms) : 0;
     return JAC_OK;
 }
 

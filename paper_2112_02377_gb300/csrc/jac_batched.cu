@@ -448,24 +448,37 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
     }
 }
 
-template <int NRHS, bool MIXED>
+template <int NRHS, bool MIXED, int NWM>
 static const void* batched_fn()
 {
-    return reinterpret_cast<const void*>(&k_batched<NRHS, 4, MIXED, 7>);
+    return reinterpret_cast<const void*>(&k_batched<NRHS, 4, MIXED, NWM>);
 }
 
-const void* batched_kernel(int nrhs, bool mixed)
+// Geometries: 224-row tiles (7 math warps + producer, 2 CTAs/SM) or 96-row
+// tiles (3 + 1 warps, 4 CTAs/SM: finer tiles for small systems).  Both leave
+// 128 registers a thread (16 warps per SM).
+const void* batched_kernel(int nrhs, bool mixed, int rows)
 {
-    switch (nrhs) {
-    case 1: return mixed ? batched_fn<1, true>() : batched_fn<1, false>();
-    case 2: return mixed ? batched_fn<2, true>() : batched_fn<2, false>();
-    case 4: return mixed ? batched_fn<4, true>() : batched_fn<4, false>();
-    default: return nullptr;
+    if (rows == 224) {
+        switch (nrhs) {
+        case 1: return mixed ? batched_fn<1, true, 7>() : batched_fn<1, false, 7>();
+        case 2: return mixed ? batched_fn<2, true, 7>() : batched_fn<2, false, 7>();
+        case 4: return mixed ? batched_fn<4, true, 7>() : batched_fn<4, false, 7>();
+        default: return nullptr;
+        }
     }
+    if (rows == 96) {
+        switch (nrhs) {
+        case 1: return mixed ? batched_fn<1, true, 3>() : batched_fn<1, false, 3>();
+        case 2: return mixed ? batched_fn<2, true, 3>() : batched_fn<2, false, 3>();
+        case 4: return mixed ? batched_fn<4, true, 3>() : batched_fn<4, false, 3>();
+        default: return nullptr;
+        }
+    }
+    return nullptr;
 }
 
-int batched_threads() { return 7 * 32 + 32; }
-int batched_rows() { return 7 * 32; }
+int batched_threads(int rows) { return rows + 32; }
 
 cudaError_t launch_batched(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
                            const DevTiles& t, const DevBatch& bt, JacCtl* ctl, int max_sweeps, cudaStream_t s)

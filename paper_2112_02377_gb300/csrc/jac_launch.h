@@ -30,10 +30,9 @@ cudaError_t launch_arm(JacCtl* ctl, int test, int mixed, int inner, long long k_
                        cudaStream_t s);
 cudaError_t launch_reset_iterate(JacCtl* ctl, cudaStream_t s);
 cudaError_t launch_reset_bar(JacCtl* ctl, cudaStream_t s);
-const void* batched_kernel(int nrhs, bool mixed);
+const void* batched_kernel(int nrhs, bool mixed, int rows);
 int batched_smem_bytes(int rows, int emax, int nrhs, int stages);
-int batched_threads();
-int batched_rows();
+int batched_threads(int rows);
 cudaError_t launch_batched(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
                            const DevTiles& t, const DevBatch& bt, JacCtl* ctl, int max_sweeps, cudaStream_t s);
 cudaError_t launch_batched_c(const double* b, const double* d, double* c, long long n, int nrhs, cudaStream_t s);

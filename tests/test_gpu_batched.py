@@ -24,11 +24,11 @@ def _batch(nsys, nrhs, seed, lo=4, hi=12):
     return mats, rhs
 
 
-@pytest.mark.parametrize("nrhs", [1, 2, 4])
-def test_batched_fp64_each_system_equals_its_own_solve(nrhs):
+@pytest.mark.parametrize("nrhs,rows", [(1, 0), (2, 0), (4, 0), (1, 96), (4, 96)])
+def test_batched_fp64_each_system_equals_its_own_solve(nrhs, rows):
     mats, rhs = _batch(23, nrhs, seed=nrhs)
     tol = 1e-8
-    ctx = J.jac_setup_batched(mats, rhs, J.opts(nrhs=nrhs, sweeps_per_graph=16))
+    ctx = J.jac_setup_batched(mats, rhs, J.opts(nrhs=nrhs, sweeps_per_graph=16, tile_rows=rows))
     try:
         k, rel, st = J.jac_solve(ctx, tol, 20000)
         assert st == J.JAC_OK
@@ -98,3 +98,24 @@ def test_batched_maxit_reports_notconv():
         assert np.all(sweeps == 30)
     finally:
         J.jac_free(ctx)
+
+
+def test_batched_autotune_picks_a_geometry_and_stays_exact():
+    mats, rhs = _batch(31, 4, seed=3, lo=8, hi=20)
+    ctx = J.jac_setup_batched(mats, rhs, J.opts(nrhs=4, autotune=1, sweeps_per_graph=7))
+    try:
+        st = J.jac_stats(ctx)
+        assert st["tile_rows"] in (96, 224) and st["ctas_per_sm"] >= 1
+        assert st["sweeps_total"] == 0
+        J.jac_sweep(ctx, 13)
+        x = J.jac_get_x(ctx)
+    finally:
+        J.jac_free(ctx)
+    off = 0
+    for A, b in zip(mats, rhs):
+        y = np.zeros((A.n, 4))
+        for _ in range(13):
+            y = O.sweep_multi(A, b, y)[0]
+        xs = x[off * 4:(off + A.n) * 4].reshape(A.n, 4)
+        assert np.linalg.norm(xs - y) <= 1e-13 * np.linalg.norm(y)
+        off += A.n

@@ -100,9 +100,11 @@ def test_per_sweep_parity_and_splitting_invariance(name, A, b, variant):
 @pytest.mark.parametrize("name,A,b", list(_cases())[:2])
 def test_variants_and_graph_batching_are_bit_identical(name, A, b):
     outs = []
-    for variant, K, rows in [(1, 64, 256), (2, 64, 256), (2, 7, 256), (2, 1, 256), (2, 64, 480), (2, 5, 480),
-                             (2, 64, 224), (3, 64, 256), (3, 3, 256), (3, 1, 256)]:
-        ctx = _setup(A, b, "bandrow", 3, variant=variant, sweeps_per_graph=K, tile_rows=rows)
+    for variant, K, rows, cps in [(1, 64, 256, 0), (2, 64, 256, 0), (2, 7, 256, 0), (2, 1, 256, 0),
+                                  (2, 64, 256, 3), (2, 64, 480, 0), (2, 5, 480, 0), (2, 64, 224, 0),
+                                  (3, 64, 256, 0), (3, 3, 256, 0), (3, 1, 256, 0), (0, 9, 0, 0)]:
+        kw = dict(autotune=1) if variant == 0 else dict(variant=variant, tile_rows=rows, ctas_per_sm=cps)
+        ctx = _setup(A, b, "bandrow", 3, sweeps_per_graph=K, **kw)
         try:
             J.jac_sweep(ctx, 23)
             J.jac_sweep(ctx, 14)
@@ -304,6 +306,30 @@ def test_grid_barrier_timeout_is_reported_and_recoverable():
         assert np.linalg.norm(x - y) <= 1e-13 * np.linalg.norm(y)
     finally:
         J.jac_free(ctx)
+
+
+def test_autotune_reports_its_choice_and_starts_from_zero():
+    A = W.laplace7(24)
+    xs, b = W.solution_and_rhs(A, 1)
+    for prec in (J.JAC_FP64, J.JAC_MIXED):
+        ctx = _setup(A, b, "bandrow_nnz", 4, autotune=1, precision=prec, inner_sweeps=16)
+        try:
+            st = J.jac_stats(ctx)
+            assert (st["variant"], st["tile_rows"]) in [(2, 256), (2, 224), (2, 480), (3, 256)]
+            assert st["ctas_per_sm"] >= 1 and st["sweeps_total"] == 0
+            x = J.jac_get_x(ctx)
+            assert not np.any(x)
+            if prec == J.JAC_FP64:
+                J.jac_sweep(ctx, 6)
+                y = np.zeros(A.n)
+                for _ in range(6):
+                    y = O.sweep(A, b, y)[0]
+                assert np.linalg.norm(J.jac_get_x(ctx) - y) <= 1e-13 * np.linalg.norm(y)
+            else:
+                k, rel, s = J.jac_solve(ctx, 1e-9, 20000)
+                assert s == J.JAC_OK and rel <= 1e-9
+        finally:
+            J.jac_free(ctx)
 
 
 # ---------------------------------------------------- mixed precision ----

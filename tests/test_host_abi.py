@@ -166,3 +166,15 @@ def test_setup_without_a_gpu_fails_loudly():
     with pytest.raises(J.JacobiError) as ei:
         J.jac_setup(A, np.ones(A.n), J.JAC_BANDROW, 2)
     assert ei.value.status == J.JAC_ECUDA
+
+
+def test_autotune_rejects_a_fixed_geometry_before_touching_the_gpu():
+    A = W.laplace7(4)
+    b = np.ones(A.n)
+    for kw in (dict(variant=2), dict(tile_rows=256), dict(ctas_per_sm=3)):
+        with pytest.raises(J.JacobiError) as e:
+            J.jac_setup(A, b, J.JAC_BANDROW, 1, J.opts(autotune=1, **kw))
+        assert "autotune" in str(e.value)
+    with pytest.raises(J.JacobiError) as e:
+        J.jac_setup_batched([A], [b], J.opts(autotune=1, tile_rows=96))
+    assert "autotune" in str(e.value)
