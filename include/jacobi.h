@@ -195,7 +195,8 @@ jac_status jac_set_b(jac_ctx* ctx, const double* b, int32_t memory);
  * jac_sweep -- apply exactly k >= 0 synchronous sweeps, no convergence test.
  *
  * Paper: one pass of Algorithm 1's loop body per sweep (q = A x, r = b - q,
- * ||r||, x += D^{-1} r) in the form of Eq. (3.4).  After the call the context
+ * ||r||, x += D^{-1} r) in the form of Eq. (3.4), carried in y = D x:
+ * y' = b + S y with S = -(L+U) D^{-1}, r = y' - y.  After the call the context
  * holds x^{k0+k}.  relres_out (may be NULL) receives the test value
  * (jac_opts.norm) of the last pre-update iterate x^{k0+k-1}
  * (unchanged if k == 0).  For JAC_MIXED contexts a sweep is one FP64 sweep.
@@ -221,7 +222,10 @@ jac_status jac_solve(jac_ctx* ctx, double tol, int64_t maxit, int64_t* sweeps_ou
                      double* relres_out);
 
 /* jac_get_x -- copy the current iterate x^k (n*nrhs, row-major, ORIGINAL row
- * order) to `x` in `memory`. */
+ * order) to `x` in `memory`.  The library carries the iterate as y = D x
+ * (D = diag(A)); jac_get_x returns x_i = y_i / a_ii with one IEEE division and
+ * jac_set_x stores y_i = a_ii x_i with one rounded multiply, so resuming from
+ * a read-back x continues from x^k to within one rounding per row. */
 jac_status jac_get_x(jac_ctx* ctx, double* x, int32_t memory);
 
 /* jac_get_history -- relres of the iterates evaluated by the last jac_sweep /

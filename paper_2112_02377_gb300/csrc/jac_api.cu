@@ -36,9 +36,9 @@ struct jac_ctx {
     // device data (new row order)
     int* d_rowptr = nullptr;
     int* d_col = nullptr;
-    double* d_T64 = nullptr;
-    float* d_T32 = nullptr;
-    double* d_c = nullptr;
+    double* d_S64 = nullptr;
+    float* d_S32 = nullptr;
+    double* d_b = nullptr;         // b in the new row order (FP64 sweep input)
     double* d_d = nullptr;
     double* d_x[2] = {nullptr, nullptr};
     float* d_e[2] = {nullptr, nullptr};
@@ -182,9 +182,9 @@ DevMat devmat(const jac_ctx* c)
     m.n = (int)c->n;
     m.rowptr = c->d_rowptr;
     m.col = c->d_col;
-    m.T64 = c->d_T64;
-    m.T32 = c->d_T32;
-    m.c = c->d_c;
+    m.S64 = c->d_S64;
+    m.S32 = c->d_S32;
+    m.b = c->d_b;
     m.d = c->d_d;
     return m;
 }
@@ -331,7 +331,7 @@ jac_status batched_restart(jac_ctx* c)
 {
     cudaStream_t s = stream_of(c);
     CK(c, launch_batched_gather_x(c->d_x[0], c->d_x[1], c->d_row_sys, c->d_mask, c->d_kpar, c->h_ctl[0].xbuf & 1,
-                                  c->n, c->nrhs, c->d_bstage, s));
+                                  c->n, c->nrhs, nullptr, c->d_bstage, s));
     CK(c, cudaMemcpyAsync(c->d_x[0], c->d_bstage, (size_t)c->n * c->nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(c, launch_batched_reset(devbatch(c), c->nrhs, s));
     CK(c, launch_reset_iterate(c->d_ctl, s));
@@ -373,7 +373,7 @@ void destroy(jac_ctx* c)
     if (c->gmix) cudaGraphExecDestroy(c->gmix);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
-    dfree(c->d_rowptr); dfree(c->d_col); dfree(c->d_T64); dfree(c->d_T32); dfree(c->d_c); dfree(c->d_d);
+    dfree(c->d_rowptr); dfree(c->d_col); dfree(c->d_S64); dfree(c->d_S32); dfree(c->d_b); dfree(c->d_d);
     dfree(c->d_x[0]); dfree(c->d_x[1]); dfree(c->d_e[0]); dfree(c->d_e[1]); dfree(c->d_dlt);
     dfree(c->d_part); dfree(c->d_ctl); dfree(c->d_hist); dfree(c->d_perm); dfree(c->d_stage); dfree(c->d_stage2);
     dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0); dfree(c->d_cta0);
@@ -600,8 +600,8 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     Plan plan;
     e = make_plan(M, s, nparts, o, plan);
     if (!e.ok()) return fail(nullptr, e.st, e.msg);
-    TForm tf;
-    e = make_tform(M, plan, tf);
+    ScaledForm tf;
+    e = make_scaled_form(M, plan, tf);
     if (!e.ok()) return fail(nullptr, e.st, e.msg);
 
     std::unique_ptr<jac_ctx, void (*)(jac_ctx*)> c(new jac_ctx(), destroy);
@@ -657,7 +657,7 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
             // 2 CTAs/SM x 4 stages for 224/256-row tiles, 1 CTA/SM x 4 stages for 480-row tiles
             stage_budget = rows <= 256 ? 26 * 1024 : 52 * 1024;
         }
-        const int64_t budget_entries = std::max<int64_t>(rows, (stage_budget - 24 * rows - 1024) / 12);
+        const int64_t budget_entries = std::max<int64_t>(rows, (stage_budget - 16 * rows - 1024) / 12);
         c->emax = (int)std::min<int64_t>(cap_entries, budget_entries);
         if (c->variant == 3) {
             c->pfn64 = halo_kernel(c->stages, false);
@@ -737,13 +737,13 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     // ---- device buffers
     CK(nullptr, dalloc(&c->d_rowptr, n + 1 + 16));
     CK(nullptr, dalloc(&c->d_col, nnz_off + 16));
-    CK(nullptr, dalloc(&c->d_T64, nnz_off + 16));
-    CK(nullptr, dalloc(&c->d_c, n + 16));
+    CK(nullptr, dalloc(&c->d_S64, nnz_off + 16));
+    CK(nullptr, dalloc(&c->d_b, n + 16));
     CK(nullptr, dalloc(&c->d_d, n + 16));
     CK(nullptr, dalloc(&c->d_x[0], n + 16));
     CK(nullptr, dalloc(&c->d_x[1], n + 16));
     if (o.precision == JAC_MIXED) {
-        CK(nullptr, dalloc(&c->d_T32, nnz_off + 16));
+        CK(nullptr, dalloc(&c->d_S32, nnz_off + 16));
         CK(nullptr, dalloc(&c->d_e[0], n + 16));
         CK(nullptr, dalloc(&c->d_e[1], n + 16));
         CK(nullptr, dalloc(&c->d_dlt, n + 16));
@@ -781,11 +781,11 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     CK(nullptr, cudaMemcpy(c->d_rowptr, tf.rowptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
     if (nnz_off) {
         CK(nullptr, cudaMemcpy(c->d_col, tf.col.data(), nnz_off * 4, cudaMemcpyHostToDevice));
-        CK(nullptr, cudaMemcpy(c->d_T64, tf.T.data(), nnz_off * 8, cudaMemcpyHostToDevice));
+        CK(nullptr, cudaMemcpy(c->d_S64, tf.S.data(), nnz_off * 8, cudaMemcpyHostToDevice));
         if (o.precision == JAC_MIXED) {
             std::vector<float> t32(nnz_off);
-            for (int64_t k = 0; k < nnz_off; ++k) t32[k] = (float)tf.T[k];
-            CK(nullptr, cudaMemcpy(c->d_T32, t32.data(), nnz_off * 4, cudaMemcpyHostToDevice));
+            for (int64_t k = 0; k < nnz_off; ++k) t32[k] = (float)tf.S[k];
+            CK(nullptr, cudaMemcpy(c->d_S32, t32.data(), nnz_off * 4, cudaMemcpyHostToDevice));
         }
     }
     CK(nullptr, cudaMemcpy(c->d_d, tf.d.data(), n * 8, cudaMemcpyHostToDevice));
@@ -807,7 +807,7 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
         st = copy_to_stage(C, b, A->memory, (size_t)n, c->d_stage);
         if (st != JAC_OK) return fail(nullptr, st, C->err);
     }
-    CK(nullptr, launch_make_c(c->d_perm, b ? c->d_stage : nullptr, c->d_d, c->d_c, (int)n, c->d_ctl, sm));
+    CK(nullptr, launch_gather_b(c->d_perm, b ? c->d_stage : nullptr, c->d_b, (int)n, c->d_ctl, sm));
     CK(nullptr, launch_reset_iterate(c->d_ctl, sm));
     CK(nullptr, launch_arm(c->d_ctl, 0, 0, o.inner_sweeps, 0, 0, -1.0, o.norm, c->d_hist, c->hist_cap, (long long)o.timeout_cycles,
                      o.fault_skip_cta, sm));
@@ -869,7 +869,7 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     DeviceGuard guard(dev);
 
     // ---- pack the systems block-diagonally in iteration-matrix form
-    TForm big;
+    ScaledForm big;
     big.rowptr.push_back(0);
     std::vector<long long> off(nsys + 1, 0);
     for (int s = 0; s < nsys; ++s) {
@@ -882,15 +882,15 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
         if (!e.ok()) return fail(nullptr, e.st, "system " + std::to_string(s) + ": " + e.msg);
         Plan p1;
         e = make_plan(M, JAC_BANDROW, 1, o, p1);
-        TForm tf;
-        if (e.ok()) e = make_tform(M, p1, tf);
+        ScaledForm tf;
+        if (e.ok()) e = make_scaled_form(M, p1, tf);
         if (!e.ok()) return fail(nullptr, e.st, "system " + std::to_string(s) + ": " + e.msg);
         const long long base = off[s], ebase = big.rowptr.back();
         if (base + M.n > INT32_MAX - 64 || ebase + (long long)tf.col.size() > INT32_MAX - 64)
             return fail(nullptr, JAC_EINVAL, "batched: packed system exceeds 2^31 rows or entries");
         for (int64_t r = 0; r < M.n; ++r) big.rowptr.push_back((int32_t)(ebase + tf.rowptr[r + 1]));
         for (size_t q = 0; q < tf.col.size(); ++q) big.col.push_back((int32_t)(tf.col[q] + base));
-        big.T.insert(big.T.end(), tf.T.begin(), tf.T.end());
+        big.S.insert(big.S.end(), tf.S.begin(), tf.S.end());
         big.d.insert(big.d.end(), tf.d.begin(), tf.d.end());
         big.max_off = std::max(big.max_off, tf.max_off);
         off[s + 1] = base + M.n;
@@ -933,7 +933,7 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     c->stages = 4;
     {
         const int64_t cap_entries = std::max<int64_t>(1, big.max_off) * rows;
-        const int64_t budget = 27 * 1024 - (int64_t)rows * (4 + 8 * nrhs + 8) - 1024;
+        const int64_t budget = 27 * 1024 - (int64_t)rows * (4 + 8 * nrhs) - 1024;
         c->emax = (int)std::min<int64_t>(cap_entries, std::max<int64_t>(rows, budget / 12));
     }
     c->pfn64 = batched_kernel(nrhs, false, rows);
@@ -981,13 +981,13 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     const size_t nv = (size_t)n * nrhs;
     CK(nullptr, dalloc(&c->d_rowptr, n + 1 + 16));
     CK(nullptr, dalloc(&c->d_col, nnz_off + 16));
-    CK(nullptr, dalloc(&c->d_T64, nnz_off + 16));
-    CK(nullptr, dalloc(&c->d_c, nv + 16 * nrhs));
+    CK(nullptr, dalloc(&c->d_S64, nnz_off + 16));
+    CK(nullptr, dalloc(&c->d_b, nv + 16 * nrhs));
     CK(nullptr, dalloc(&c->d_d, n + 16));
     CK(nullptr, dalloc(&c->d_x[0], nv + 16 * nrhs));
     CK(nullptr, dalloc(&c->d_x[1], nv + 16 * nrhs));
     if (o.precision == JAC_MIXED) {
-        CK(nullptr, dalloc(&c->d_T32, nnz_off + 16));
+        CK(nullptr, dalloc(&c->d_S32, nnz_off + 16));
         CK(nullptr, dalloc(&c->d_e[0], nv + 16 * nrhs));
         CK(nullptr, dalloc(&c->d_e[1], nv + 16 * nrhs));
         CK(nullptr, dalloc(&c->d_dlt, nv + 16 * nrhs));
@@ -1026,11 +1026,11 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
         for (long long r = off[s]; r < off[s + 1]; ++r) row_sys[r] = s;
     CK(nullptr, up(c->d_rowptr, big.rowptr.data(), (n + 1) * 4));
     CK(nullptr, up(c->d_col, big.col.data(), nnz_off * 4));
-    CK(nullptr, up(c->d_T64, big.T.data(), nnz_off * 8));
+    CK(nullptr, up(c->d_S64, big.S.data(), nnz_off * 8));
     if (o.precision == JAC_MIXED && nnz_off) {
         std::vector<float> t32(nnz_off);
-        for (int64_t q = 0; q < nnz_off; ++q) t32[q] = (float)big.T[q];
-        CK(nullptr, up(c->d_T32, t32.data(), nnz_off * 4));
+        for (int64_t q = 0; q < nnz_off; ++q) t32[q] = (float)big.S[q];
+        CK(nullptr, up(c->d_S32, t32.data(), nnz_off * 4));
     }
     CK(nullptr, up(c->d_d, big.d.data(), n * 8));
     CK(nullptr, up(c->d_row0, tl.row0.data(), tl.row0.size() * 4));
@@ -1056,7 +1056,7 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
                                         sm));
         }
     }
-    CK(nullptr, launch_batched_c(c->d_bstage, c->d_d, c->d_c, n, nrhs, sm));
+    CK(nullptr, cudaMemcpyAsync(c->d_b, c->d_bstage, (size_t)n * nrhs * 8, cudaMemcpyDeviceToDevice, sm));
     CK(nullptr, launch_batched_bnorm(c->d_bstage, c->d_sys_off, nsys, nrhs, c->d_bnorm, sm));
     CK(nullptr, launch_batched_reset(devbatch(C), nrhs, sm));
     CK(nullptr, launch_reset_iterate(c->d_ctl, sm));
@@ -1079,6 +1079,7 @@ jac_status jac_set_x(jac_ctx* c, const double* x, int32_t memory)
             if (memory != JAC_MEM_HOST && memory != JAC_MEM_DEVICE) return fail(c, JAC_EINVAL, "bad memory");
             CK(c, cudaMemcpyAsync(c->d_x[0], x, cnt * 8,
                                   memory == JAC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+            CK(c, launch_batched_scale(c->d_x[0], c->d_d, c->n, c->nrhs, s));
         } else {
             CK(c, cudaMemsetAsync(c->d_x[0], 0, cnt * 8, s));
         }
@@ -1093,7 +1094,7 @@ jac_status jac_set_x(jac_ctx* c, const double* x, int32_t memory)
         jac_status st = copy_to_stage(c, x, memory, (size_t)c->n, c->d_stage);
         if (st != JAC_OK) return st;
     }
-    CK(c, launch_gather_rows(c->d_perm, x ? c->d_stage : nullptr, c->d_x[0], (int)c->n, 1, s));
+    CK(c, launch_gather_rows(c->d_perm, x ? c->d_stage : nullptr, c->d_d, c->d_x[0], (int)c->n, 1, s));
     CK(c, launch_reset_iterate(c->d_ctl, s));
     if (fetch_ctl(c, &c->h_ctl[0]) != JAC_OK) return JAC_ECUDA;
     CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
@@ -1111,7 +1112,7 @@ jac_status jac_set_b(jac_ctx* c, const double* b, int32_t memory)
         if (b) CK(c, cudaMemcpyAsync(c->d_bstage, b, cnt * 8,
                                      memory == JAC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         else CK(c, cudaMemsetAsync(c->d_bstage, 0, cnt * 8, s));
-        CK(c, launch_batched_c(c->d_bstage, c->d_d, c->d_c, c->n, c->nrhs, s));
+        CK(c, cudaMemcpyAsync(c->d_b, c->d_bstage, cnt * 8, cudaMemcpyDeviceToDevice, s));
         CK(c, launch_batched_bnorm(c->d_bstage, c->d_sys_off, c->nsys, c->nrhs, c->d_bnorm, s));
         CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
         return JAC_OK;
@@ -1120,7 +1121,7 @@ jac_status jac_set_b(jac_ctx* c, const double* b, int32_t memory)
         jac_status st = copy_to_stage(c, b, memory, (size_t)c->n, c->d_stage);
         if (st != JAC_OK) return st;
     }
-    CK(c, launch_make_c(c->d_perm, b ? c->d_stage : nullptr, c->d_d, c->d_c, (int)c->n, c->d_ctl, s));
+    CK(c, launch_gather_b(c->d_perm, b ? c->d_stage : nullptr, c->d_b, (int)c->n, c->d_ctl, s));
     CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
     return JAC_OK;
 }
@@ -1274,9 +1275,9 @@ jac_status jac_get_x(jac_ctx* c, double* x, int32_t memory)
         src = c->d_bstage;
         cnt = (size_t)c->n * c->nrhs;
         CK(c, launch_batched_gather_x(c->d_x[0], c->d_x[1], c->d_row_sys, c->d_mask, c->d_kpar, xb, c->n, c->nrhs,
-                                      src, s));
+                                      c->d_d, src, s));
     } else {
-        CK(c, launch_scatter_rows(c->d_perm, c->d_x[xb], c->d_stage, (int)c->n, 1, s));
+        CK(c, launch_scatter_rows(c->d_perm, c->d_x[xb], c->d_d, c->d_stage, (int)c->n, 1, s));
     }
     if (memory == JAC_MEM_DEVICE) {
         CK(c, cudaMemcpyAsync(x, src, cnt * sizeof(double), cudaMemcpyDeviceToDevice, s));

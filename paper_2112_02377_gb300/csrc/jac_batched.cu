@@ -35,7 +35,7 @@ __device__ __forceinline__ void mbar_arrive_b(uint64_t* bar)
 }
 
 struct BStageLayout {
-    int o_val, o_col, o_rp, o_c, o_d, bytes;
+    int o_val, o_col, o_rp, o_c, bytes;   // o_c: the tile's b, NRHS per row (FP64 phases)
 };
 
 __host__ __device__ inline BStageLayout bstage_layout(int rows, int emax, int nrhs)
@@ -46,8 +46,7 @@ __host__ __device__ inline BStageLayout bstage_layout(int rows, int emax, int nr
     L.o_col = L.o_val + up((emax + 4) * 8);
     L.o_rp = L.o_col + up((emax + 8) * 4);
     L.o_c = L.o_rp + up((rows + 12) * 4);
-    L.o_d = L.o_c + up((rows + 4) * nrhs * 8);
-    L.bytes = L.o_d + up((rows + 4) * 8);
+    L.bytes = L.o_c + up((rows + 4) * nrhs * 8);
     return L;
 }
 
@@ -216,20 +215,18 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
                 const int rb = r0 & ~3, re = (r1 + 1 + 3) & ~3;
                 bytes += (unsigned)(re - rb) * 4u;
                 const int hb = r0 & ~1, he = (r1 + 1) & ~1;
-                if (fp64) bytes += (unsigned)(he - hb) * 8u * (NRHS + 1);
+                if (fp64) bytes += (unsigned)(he - hb) * 8u * NRHS;
                 mbar_expect_tx(bar, bytes);
                 if (!over) {
                     if (ve > vb) {
-                        if (fp64) bulk_g2s(st + L.o_val, m.T64 + vb, (unsigned)(ve - vb) * 8u, bar, pol);
-                        else bulk_g2s(st + L.o_val, m.T32 + vb, (unsigned)(ve - vb) * 4u, bar, pol);
+                        if (fp64) bulk_g2s(st + L.o_val, m.S64 + vb, (unsigned)(ve - vb) * 8u, bar, pol);
+                        else bulk_g2s(st + L.o_val, m.S32 + vb, (unsigned)(ve - vb) * 4u, bar, pol);
                     }
                     if (ce > cb) bulk_g2s(st + L.o_col, m.col + cb, (unsigned)(ce - cb) * 4u, bar, pol);
                 }
                 bulk_g2s(st + L.o_rp, m.rowptr + rb, (unsigned)(re - rb) * 4u, bar, pol);
-                if (fp64 && he > hb) {
-                    bulk_g2s(st + L.o_c, m.c + (size_t)hb * NRHS, (unsigned)(he - hb) * 8u * NRHS, bar, pol);
-                    bulk_g2s(st + L.o_d, m.d + hb, (unsigned)(he - hb) * 8u, bar, pol);
-                }
+                if (fp64 && he > hb)
+                    bulk_g2s(st + L.o_c, m.b + (size_t)hb * NRHS, (unsigned)(he - hb) * 8u * NRHS, bar, pol);
                 issued = j + 1;
             }
             const long long t0 = clock64();
@@ -351,7 +348,6 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
                 if (norm_ph) {
                     const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
                     const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (size_t)(r0 & ~1) * NRHS;
-                    const double* sd = reinterpret_cast<const double*>(st + L.o_d) - (r0 & ~1);
                     double acc[NRHS], xi[NRHS];
 #pragma unroll
                     for (int q = 0; q < NRHS; ++q) { acc[q] = in ? sc[(size_t)r * NRHS + q] : 0.0; xi[q] = 0.0; }
@@ -359,10 +355,9 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
                     if (!over)
                         brow_dot<NRHS>(acc, kb, len, xs, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; });
                     else
-                        brow_dot<NRHS>(acc, kb, len, xs, [&](int e) { return __ldg(m.T64 + e); },
+                        brow_dot<NRHS>(acc, kb, len, xs, [&](int e) { return __ldg(m.S64 + e); },
                                        [&](int e) { return __ldg(m.col + e); });
                     if (in) {
-                        const double di = sd[r];
 #pragma unroll
                         for (int q = 0; q < NRHS; ++q) {
                             if (msk & (1 << q)) continue;        // stopped: its iterate stays where it is
@@ -373,7 +368,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
                                 __stcg(v.dlt + (size_t)r * NRHS + q, dl);
                                 __stcg(v.e[1] + (size_t)r * NRHS + q, dl);
                             }
-                            accumulate_residual(acc[q], xi[q], di, ss[q], mx[q]);
+                            accumulate_residual(acc[q], xi[q], ss[q], mx[q]);
                         }
                     }
                 } else {
@@ -385,7 +380,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
                     if (!over)
                         brow_dot<NRHS>(acc, kb, len, es, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; });
                     else
-                        brow_dot<NRHS>(acc, kb, len, es, [&](int e) { return __ldg(m.T32 + e); },
+                        brow_dot<NRHS>(acc, kb, len, es, [&](int e) { return __ldg(m.S32 + e); },
                                        [&](int e) { return __ldg(m.col + e); });
                     if (in) {
 #pragma unroll
@@ -499,13 +494,12 @@ cudaError_t launch_batched(const void* fn, int grid, int threads, int smem, cons
 
 // ----------------------------------------------------------- helpers
 
-// c[r][q] = b_perm(r)[q] / a_rr for the packed systems (identity permutation).
-__global__ void k_batched_c(const double* __restrict__ b, const double* __restrict__ d, double* __restrict__ c,
-                            long long n, int nrhs)
+// x -> iterate y[r][q] = a_rr x[r][q] in place (packed systems, identity order).
+__global__ void k_batched_scale(double* __restrict__ x, const double* __restrict__ d, long long n, int nrhs)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * nrhs) return;
-    c[i] = __ddiv_rn(b[i], d[i / nrhs]);
+    x[i] = __dmul_rn(d[i / nrhs], x[i]);
 }
 
 // ||b_s,q||_2 for every system (one CTA per system, fixed order).
@@ -530,10 +524,13 @@ __global__ void __launch_bounds__(256) k_batched_bnorm(const double* __restrict_
     }
 }
 
-// x_out[r][q] = x[kpar(s,q)][r][q]: each right-hand side from the buffer that holds its final iterate.
+// Result read-back: each (row, right-hand side) from the buffer that holds its
+// reported iterate, converted back from y to x = y / a_rr (IEEE division;
+// d == nullptr: y itself).
 __global__ void k_batched_gather_x(const double* __restrict__ x0, const double* __restrict__ x1,
                                    const int* __restrict__ row_sys, const int* __restrict__ mask,
-                                   const int* __restrict__ kpar, int cur, long long n, int nrhs, double* __restrict__ out)
+                                   const int* __restrict__ kpar, int cur, long long n, int nrhs,
+                                   const double* __restrict__ d, double* __restrict__ out)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * nrhs) return;
@@ -541,7 +538,8 @@ __global__ void k_batched_gather_x(const double* __restrict__ x0, const double* 
     const int q = (int)(i - r * nrhs);
     const int s = row_sys[r];
     const int p = (mask[s] >> q) & 1 ? kpar[s * nrhs + q] : cur;
-    out[i] = (p & 1) ? x1[i] : x0[i];
+    const double y = (p & 1) ? x1[i] : x0[i];
+    out[i] = d ? __ddiv_rn(y, d[r]) : y;
 }
 
 __global__ void k_batched_reset(int* mask, long long* ksys, double* rel, int* kpar, int* sys_status, unsigned* cnt,
@@ -562,10 +560,10 @@ __global__ void k_batched_reset(int* mask, long long* ksys, double* rel, int* kp
     if (i == 0) *ndone = 0;
 }
 
-cudaError_t launch_batched_c(const double* b, const double* d, double* c, long long n, int nrhs, cudaStream_t s)
+cudaError_t launch_batched_scale(double* x, const double* d, long long n, int nrhs, cudaStream_t s)
 {
     const long long tot = n * nrhs;
-    k_batched_c<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(b, d, c, n, nrhs);
+    k_batched_scale<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x, d, n, nrhs);
     return cudaGetLastError();
 }
 
@@ -577,10 +575,12 @@ cudaError_t launch_batched_bnorm(const double* b, const long long* off, int nsys
 }
 
 cudaError_t launch_batched_gather_x(const double* x0, const double* x1, const int* row_sys, const int* mask,
-                                    const int* kpar, int cur, long long n, int nrhs, double* out, cudaStream_t s)
+                                    const int* kpar, int cur, long long n, int nrhs, const double* d, double* out,
+                                    cudaStream_t s)
 {
     const long long tot = n * nrhs;
-    k_batched_gather_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x0, x1, row_sys, mask, kpar, cur, n, nrhs, out);
+    k_batched_gather_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(x0, x1, row_sys, mask, kpar, cur, n, nrhs, d,
+                                                                        out);
     return cudaGetLastError();
 }
 

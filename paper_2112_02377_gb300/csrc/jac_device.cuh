@@ -11,9 +11,10 @@ namespace jac {
 enum : int { ST_TIMEOUT = 1, ST_NUMERIC = 2 };
 // JacCtl::done values.
 enum : int { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_LIMIT = 2, DONE_NUMERIC = 3 };
-// Sweep phases.  P64: plain FP64 Jacobi sweep.  P64R: FP64 residual pass of
-// the mixed refinement (writes delta = D^{-1} r, no update of x).  P32: FP32
-// inner sweep e' = delta + T e.  P32L: last inner sweep, fused x += e.
+// Sweep phases, in the diagonally scaled variables y = D x, f = D e (see
+// DevMat).  P64: plain FP64 Jacobi sweep.  P64R: FP64 residual pass of the
+// mixed refinement (writes r = b - A x in FP32, no update of y).  P32: FP32
+// inner sweep f' = r + S f.  P32L: last inner sweep, fused y += f.
 enum : int { PH_P64 = 0, PH_P64R = 1, PH_P32 = 2, PH_P32L = 3 };
 
 // Control block in device memory.  Kernels read it at start and the last /
@@ -48,21 +49,25 @@ struct Partial {
     unsigned long long mx;    // max |r_i| as IEEE bits (order-preserving for |r|)
 };
 
-// Off-diagonal iteration-matrix data in the new row order (constant during a solve).
+// Off-diagonal iteration-matrix data in the new row order (constant during a
+// solve).  The kernels iterate on y = D x: the Jacobi step
+//   x'_i = (b_i - sum_{j != i} a_ij x_j) / a_ii
+// multiplied by a_ii reads y'_i = b_i + sum_{j != i} S_ij y_j with
+// S_ij = -a_ij / a_jj, and the residual of the iterate is r_i = y'_i - y_i.
 struct DevMat {
     int n;
     const int* rowptr;        // n+1 (+pad)
     const int* col;           // nnz_off (+pad)
-    const double* T64;        // nnz_off (+pad)
-    const float* T32;         // nnz_off (+pad), mixed only
-    const double* c;          // n (+pad): b_i / a_ii
-    const double* d;          // n (+pad): a_ii
+    const double* S64;        // nnz_off (+pad): -a_ij / a_jj
+    const float* S32;         // nnz_off (+pad), mixed only
+    const double* b;          // n (+pad): right-hand side in the new order
+    const double* d;          // n (+pad): a_ii (conversions x <-> y only)
 };
 
 struct DevVec {
-    double* x[2];             // FP64 iterate, ping-pong
-    float* e[2];              // FP32 inner iterate, ping-pong (mixed)
-    float* dlt;               // FP32 delta = D^{-1} r (mixed)
+    double* x[2];             // FP64 iterate y = D x, ping-pong
+    float* e[2];              // FP32 inner iterate f = D e, ping-pong (mixed)
+    float* dlt;               // FP32 residual r of the last P64R pass (mixed)
     Partial* part;            // [2][nslots] per-sweep partial norms
     int nslots;
     unsigned long long* trace;  // [ctas][4]: compute ns, barrier-wait ns, sweeps, 0 (persistent kernels)
@@ -126,19 +131,17 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v)
     return v;
 }
 
-// Residual bookkeeping of one row from its update: r = a_ii (x' - x).
-__device__ __forceinline__ void accumulate_residual(double xnew, double xold, double di, double& ss,
-                                                    unsigned long long& mx)
+// Residual bookkeeping of one row from its update: r = y' - y = (b - A x)_i.
+__device__ __forceinline__ void accumulate_residual(double ynew, double yold, double& ss, unsigned long long& mx)
 {
-    const double dl = __dadd_rn(xnew, -xold);
-    const double r = __dmul_rn(di, dl);
+    const double r = __dadd_rn(ynew, -yold);
     ss = __fma_rn(r, r, ss);
     mx = umax64(mx, abs_bits(r));
 }
 
 // Phase of a sweep: plain FP64 sweeps, or position `pos` in the mixed
 // refinement cycle of `inner` sweeps (FP64 residual pass, FP32 inner sweeps,
-// last inner sweep fused with x += e).
+// last inner sweep fused with y += f).
 __device__ __forceinline__ int phase_of(bool mixed, int pos, int inner)
 {
     if (!mixed) return PH_P64;

@@ -28,15 +28,17 @@ struct Plan {
     int64_t nparts() const { return (int64_t)part_ptr.size() - 1; }
 };
 
-// Off-diagonal part of P A P^T in the iteration-matrix form of Sec. 3:
-//   x'_i = c_i + sum_j T_ij x_j,  T_ij = -a_ij / a_ii,  c_i = b_i / a_ii,
+// Off-diagonal part of P A P^T for the Jacobi iteration of Sec. 3 carried in
+// the diagonally scaled iterate y = D x:
+//   y'_i = b_i + sum_j S_ij y_j,  S_ij = -a_ij / a_jj   (so y' = D x' with
+//   x' = D^{-1}(b - (L+U) x)),  residual r_i = y'_i - y_i,
 // rows in the new order, each row's entries in the ORIGINAL stored order with
 // columns renumbered to the new order.  d_i = a_ii.
-struct TForm {
+struct ScaledForm {
     int64_t n = 0;
     std::vector<int32_t> rowptr;    // n+1 (off-diagonal entries only)
     std::vector<int32_t> col;       // new column indices
-    std::vector<double> T;          // -a_ij / a_ii
+    std::vector<double> S;          // -a_ij / a_jj (iteration on y = D x)
     std::vector<double> d;          // a_ii (new order)
     int64_t max_off = 0;            // longest off-diagonal row
 };
@@ -47,7 +49,7 @@ struct Tiling {
     int32_t rows_per_tile = 256;
     int32_t max_entries = 0;            // cap of off-diagonal entries in a staged tile
     std::vector<int32_t> row0;          // ntiles+1 tile row boundaries
-    std::vector<int32_t> nnz0;          // ntiles+1: T-form rowptr at the boundaries
+    std::vector<int32_t> nnz0;          // ntiles+1: off-diagonal rowptr at the boundaries
     std::vector<int32_t> cta0;          // ctas+1 tile ranges per CTA
     std::vector<int32_t> tile_part;     // partition of each tile
     int64_t ntiles() const { return (int64_t)row0.size() - 1; }
@@ -81,12 +83,12 @@ struct Error {
 // jac_partition.cpp
 Error host_csr_from_abi(const jac_csr* A, bool transpose, HostCSR& out);   // A must be host memory
 Error make_plan(const HostCSR& A, jac_splitting s, int32_t nparts, const jac_opts& o, Plan& plan);
-Error make_tform(const HostCSR& A, const Plan& plan, TForm& tf);
+Error make_scaled_form(const HostCSR& A, const Plan& plan, ScaledForm& tf);
 void dependency_lists(const HostCSR& A, const Plan& plan, std::vector<int64_t>& recv_ptr,
                       std::vector<int32_t>& recv_from, std::vector<int64_t>& recv);
-void make_tiling(const TForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
+void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
                  int64_t ctas, Tiling& t);
 HostCSR transpose_csr(const HostCSR& A);
-void make_windows(const TForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w);
+void make_windows(const ScaledForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w);
 
 }  // namespace jac

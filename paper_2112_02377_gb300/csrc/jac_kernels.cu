@@ -1,11 +1,14 @@
 // Sweep kernels of the GB300 Jacobi library.
 //
-// Both kernels evaluate, for every row i of the (reordered) matrix,
-//   x'_i = c_i + sum_{j != i} T_ij x_j          (Sec. 3, Eq. (3.4) with
-//                                                 T = -D^{-1}(L+U), c = D^{-1} b)
-//   r_i  = a_ii (x'_i - x_i)  = (b - A x)_i      (Algorithm 1's residual of x^k)
-// and fuse the reductions sum r_i^2 and max |r_i| (Algorithm 1's norm; the
-// paper's dot products use MPI_ALLREDUCE, Sec. 4.2.2, here a grid reduction).
+// The kernels evaluate the Jacobi step of Sec. 3, Eq. (3.4),
+// x' = D^{-1}(b - (L+U) x), in the diagonally scaled iterate y = D x:
+//   y'_i = b_i + sum_{j != i} S_ij y_j,   S_ij = -a_ij / a_jj
+//   r_i  = y'_i - y_i  = (b - A x)_i      (Algorithm 1's residual of x^k)
+// (the same iteration: y' = D x' exactly in real arithmetic; S = D T D^{-1}
+// with T = -D^{-1}(L+U)), and fuse the reductions sum r_i^2 and max |r_i|
+// (Algorithm 1's norm; the paper's dot products use MPI_ALLREDUCE, Sec. 4.2.2,
+// here a grid reduction).  Carrying y instead of x saves the multiply by a_ii
+// in the residual and the diagonal's 8 bytes per row in every sweep.
 // The off-diagonal terms of a row are accumulated by one thread in the stored
 // order with fused multiply-adds, so the iterate depends only on the row and
 // never on the splitting, tiling or CTA that computes it.
@@ -133,9 +136,9 @@ __global__ void __launch_bounds__(256) k_row_sweep(DevMat m, DevVec v, JacCtl* c
         if (PH == PH_P64 || PH == PH_P64R) {
             const double* xs = v.x[xb];
             const double xi = __ldcg(xs + i);
-            double acc1[1] = {__ldg(m.c + i)};
+            double acc1[1] = {__ldg(m.b + i)};
             const int kb1[1] = {kb}, len1[1] = {ke - kb};
-            rows_dot<1>(acc1, kb1, len1, [&](int k) { return __ldg(m.T64 + k); },
+            rows_dot<1>(acc1, kb1, len1, [&](int k) { return __ldg(m.S64 + k); },
                         [&](int k) { return __ldcg(xs + ldc(k)); });
             const double acc = acc1[0];
             if (PH == PH_P64) {
@@ -145,13 +148,13 @@ __global__ void __launch_bounds__(256) k_row_sweep(DevMat m, DevVec v, JacCtl* c
                 v.dlt[i] = dl;
                 v.e[1][i] = dl;
             }
-            accumulate_residual(acc, xi, __ldg(m.d + i), ss, mx);
+            accumulate_residual(acc, xi, ss, mx);
         } else {
             const int j = s_phase;   // inner step: e_j -> e_{j+1}
             const float* es = v.e[j & 1];
             float acc1[1] = {__ldcg(v.dlt + i)};
             const int kb1[1] = {kb}, len1[1] = {ke - kb};
-            rows_dot<1>(acc1, kb1, len1, [&](int k) { return __ldg(m.T32 + k); },
+            rows_dot<1>(acc1, kb1, len1, [&](int k) { return __ldg(m.S32 + k); },
                         [&](int k) { return __ldcg(es + ldc(k)); });
             const float acc = acc1[0];
             if (PH == PH_P32) v.e[(j + 1) & 1][i] = acc;
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(256) k_row_sweep(DevMat m, DevVec v, JacCtl* c
 // =========================================================================
 
 struct StageLayout {
-    int o_val, o_col, o_rp, o_c, o_d, bytes;
+    int o_val, o_col, o_rp, o_c, bytes;   // o_c: the tile's b (FP64 phases)
 };
 
 __host__ __device__ inline StageLayout stage_layout(int rows, int emax)
@@ -243,8 +246,7 @@ __host__ __device__ inline StageLayout stage_layout(int rows, int emax)
     L.o_col = L.o_val + up((emax + 4) * 8);
     L.o_rp = L.o_col + up((emax + 8) * 4);
     L.o_c = L.o_rp + up((rows + 12) * 4);
-    L.o_d = L.o_c + up((rows + 4) * 8);
-    L.bytes = L.o_d + up((rows + 4) * 8);
+    L.bytes = L.o_c + up((rows + 4) * 8);
     return L;
 }
 
@@ -371,21 +373,18 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                 const int rb = r0 & ~3, re = (r1 + 1 + 3) & ~3;
                 bytes += (unsigned)(re - rb) * 4u;
                 const int hb = r0 & ~1, he = (r1 + 1) & ~1;
-                if (fp64) bytes += 2u * (unsigned)(he - hb) * 8u;
+                if (fp64) bytes += (unsigned)(he - hb) * 8u;
                 uint64_t* bar = &full[sidx];
                 mbar_expect_tx(bar, bytes);
                 if (!over) {
                     if (ve > vb) {
-                        if (fp64) bulk_g2s(st + L.o_val, m.T64 + vb, (unsigned)(ve - vb) * 8u, bar, pol);
-                        else bulk_g2s(st + L.o_val, m.T32 + vb, (unsigned)(ve - vb) * 4u, bar, pol);
+                        if (fp64) bulk_g2s(st + L.o_val, m.S64 + vb, (unsigned)(ve - vb) * 8u, bar, pol);
+                        else bulk_g2s(st + L.o_val, m.S32 + vb, (unsigned)(ve - vb) * 4u, bar, pol);
                     }
                     if (ce > cb) bulk_g2s(st + L.o_col, m.col + cb, (unsigned)(ce - cb) * 4u, bar, pol);
                 }
                 bulk_g2s(st + L.o_rp, m.rowptr + rb, (unsigned)(re - rb) * 4u, bar, pol);
-                if (fp64 && he > hb) {
-                    bulk_g2s(st + L.o_c, m.c + hb, (unsigned)(he - hb) * 8u, bar, pol);
-                    bulk_g2s(st + L.o_d, m.d + hb, (unsigned)(he - hb) * 8u, bar, pol);
-                }
+                if (fp64 && he > hb) bulk_g2s(st + L.o_c, m.b + hb, (unsigned)(he - hb) * 8u, bar, pol);
                 issued = j + 1;
             }
             // Drain: the last min(STAGES, issued) jobs occupy distinct stages;
@@ -495,12 +494,11 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                         }
                         if (lmax > PF && cur.len > PF) acc = row_tail(sv, scol, src, cur.kb + PF, cur.len - PF, acc);
                     } else if (cur.in) {
-                        acc = row_global(F64 ? reinterpret_cast<const Real*>(m.T64) : reinterpret_cast<const Real*>(m.T32),
+                        acc = row_global(F64 ? reinterpret_cast<const Real*>(m.S64) : reinterpret_cast<const Real*>(m.S32),
                                          m.col, src, cur.kb, cur.len, acc);
                     }
                     if (cur.in) {
                         if constexpr (F64) {
-                            const double* sd = reinterpret_cast<const double*>(st + L.o_d) - (cur.r0 & ~1);
                             if (ph == PH_P64) {
                                 __stcg(xd + r, (double)acc);
                             } else {
@@ -508,7 +506,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                                 __stcg(v.dlt + r, dl);
                                 __stcg(v.e[1] + r, dl);
                             }
-                            accumulate_residual((double)acc, (double)cur.xi, sd[r], ss, mx);
+                            accumulate_residual((double)acc, (double)cur.xi, ss, mx);
                         } else {
                             if (ph == PH_P32) __stcg(ed + r, (float)acc);
                             else __stcg(v.x[xb] + r, __dadd_rn(__ldcg(v.x[xb] + r), (double)acc));
@@ -540,14 +538,13 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                     if (norm_ph) {
                         const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
                         const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
-                        const double* sd = reinterpret_cast<const double*>(st + L.o_d) - (r0 & ~1);
                         const double xi = in ? __ldcg(xs + r) : 0.0;
                         double a1[1] = {in ? sc[r] : 0.0};
                         if (!over)
                             rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
                                         [&](int e) { return __ldcg(xs + scol[e]); });
                         else if (in)
-                            a1[0] = row_global(m.T64, m.col, xs, kb1[0], len1[0], a1[0]);
+                            a1[0] = row_global(m.S64, m.col, xs, kb1[0], len1[0], a1[0]);
                         if (in) {
                             if (ph == PH_P64) {
                                 __stcg(xd + r, a1[0]);
@@ -556,7 +553,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                                 __stcg(v.dlt + r, dl);
                                 __stcg(v.e[1] + r, dl);
                             }
-                            accumulate_residual(a1[0], xi, sd[r], ss, mx);
+                            accumulate_residual(a1[0], xi, ss, mx);
                         }
                     } else {
                         const float* sv = reinterpret_cast<const float*>(st + L.o_val) - (p0 & ~3);
@@ -565,7 +562,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                             rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
                                         [&](int e) { return __ldcg(es + scol[e]); });
                         else if (in)
-                            a1[0] = row_global(m.T32, m.col, es, kb1[0], len1[0], a1[0]);
+                            a1[0] = row_global(m.S32, m.col, es, kb1[0], len1[0], a1[0]);
                         if (in) {
                             if (ph == PH_P32) __stcg(ed + r, a1[0]);
                             else __stcg(v.x[xb] + r, __dadd_rn(__ldcg(v.x[xb] + r), (double)a1[0]));
@@ -683,7 +680,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
 // =========================================================================
 
 struct HaloLayout {
-    int o_val, o_col, o_rp, o_c, o_d, o_x, bytes;
+    int o_val, o_col, o_rp, o_c, o_x, bytes;
 };
 
 __host__ __device__ inline HaloLayout halo_layout(int rows, int emax, int xcap)
@@ -694,8 +691,7 @@ __host__ __device__ inline HaloLayout halo_layout(int rows, int emax, int xcap)
     L.o_col = L.o_val + up((emax + 4) * 8);
     L.o_rp = L.o_col + up((emax + 8) * 4);
     L.o_c = L.o_rp + up((rows + 12) * 4);
-    L.o_d = L.o_c + up((rows + 4) * 8);
-    L.o_x = L.o_d + up((rows + 4) * 8);
+    L.o_x = L.o_c + up((rows + 4) * 8);
     L.bytes = L.o_x + up((xcap + 8) * 8);
     return L;
 }
@@ -838,23 +834,20 @@ k_halo(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                         const int rb = r0 & ~3, re = (r1 + 1 + 3) & ~3;
                         bytes += (unsigned)(re - rb) * 4u;
                         const int hb = r0 & ~1, he = (r1 + 1) & ~1;
-                        if (fp64) bytes += 2u * (unsigned)(he - hb) * 8u;
+                        if (fp64) bytes += (unsigned)(he - hb) * 8u;
                         uint64_t* bar = &fmat[sidx];
                         mbar_expect_tx(bar, bytes);
                         // windowed tiles read tile-local columns, fallback tiles global ones
                         const int* colsrc = (h.w & 1) ? m.col : t.lcol;
                         if (!over) {
                             if (ve > vb) {
-                                if (fp64) bulk_g2s(st + L.o_val, m.T64 + vb, (unsigned)(ve - vb) * 8u, bar, pol);
-                                else bulk_g2s(st + L.o_val, m.T32 + vb, (unsigned)(ve - vb) * 4u, bar, pol);
+                                if (fp64) bulk_g2s(st + L.o_val, m.S64 + vb, (unsigned)(ve - vb) * 8u, bar, pol);
+                                else bulk_g2s(st + L.o_val, m.S32 + vb, (unsigned)(ve - vb) * 4u, bar, pol);
                             }
                             if (ce > cb) bulk_g2s(st + L.o_col, colsrc + cb, (unsigned)(ce - cb) * 4u, bar, pol);
                         }
                         bulk_g2s(st + L.o_rp, m.rowptr + rb, (unsigned)(re - rb) * 4u, bar, pol);
-                        if (fp64 && he > hb) {
-                            bulk_g2s(st + L.o_c, m.c + hb, (unsigned)(he - hb) * 8u, bar, pol);
-                            bulk_g2s(st + L.o_d, m.d + hb, (unsigned)(he - hb) * 8u, bar, pol);
-                        }
+                        if (fp64 && he > hb) bulk_g2s(st + L.o_c, m.b + hb, (unsigned)(he - hb) * 8u, bar, pol);
                         ++jm;
                         prog = true;
                     }
@@ -967,7 +960,6 @@ k_halo(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                 if (norm_ph) {
                     const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
                     const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
-                    const double* sd = reinterpret_cast<const double*>(st + L.o_d) - (r0 & ~1);
                     const double* sx = reinterpret_cast<const double*>(st + L.o_x);
                     double acc = in ? sc[r] : 0.0;
                     double xi = 0.0;
@@ -982,7 +974,7 @@ k_halo(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                             rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
                                         [&](int e) { return __ldcg(xs + scol[e]); });
                         else
-                            rows_dot<1>(a1, kb1, len1, [&](int e) { return __ldg(m.T64 + e); },
+                            rows_dot<1>(a1, kb1, len1, [&](int e) { return __ldg(m.S64 + e); },
                                         [&](int e) { return __ldcg(xs + __ldg(m.col + e)); });
                     }
                     acc = a1[0];
@@ -994,7 +986,7 @@ k_halo(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                             __stcg(v.dlt + r, dl);
                             __stcg(v.e[1] + r, dl);
                         }
-                        accumulate_residual(acc, xi, sd[r], ss, mx);
+                        accumulate_residual(acc, xi, ss, mx);
                     }
                 } else {
                     const float* sv = reinterpret_cast<const float*>(st + L.o_val) - (p0 & ~3);
@@ -1008,7 +1000,7 @@ k_halo(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                         rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
                                     [&](int e) { return __ldcg(es + scol[e]); });
                     else
-                        rows_dot<1>(a1, kb1, len1, [&](int e) { return __ldg(m.T32 + e); },
+                        rows_dot<1>(a1, kb1, len1, [&](int e) { return __ldg(m.S32 + e); },
                                     [&](int e) { return __ldcg(es + __ldg(m.col + e)); });
                     acc = a1[0];
                     if (in) {
@@ -1129,31 +1121,36 @@ const void* halo_kernel(int stages, bool mixed)
 // =========================================================================
 
 // dst[r*nrhs + c] = src[perm[r]*nrhs + c] (src may be NULL = zero)
+// x (caller's row order) -> iterate y_r = a_rr x_perm(r) in the new order
+// (d == nullptr: no scaling; src == nullptr: zero).
 __global__ void k_gather_rows(const long long* __restrict__ perm, const double* __restrict__ src,
-                              double* __restrict__ dst, int n, int nrhs)
+                              const double* __restrict__ d, double* __restrict__ dst, int n, int nrhs)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n * nrhs) return;
     const int r = (int)(idx / nrhs), c = (int)(idx - (long long)r * nrhs);
-    dst[idx] = src ? src[perm[r] * nrhs + c] : 0.0;
+    const double v = src ? src[perm[r] * nrhs + c] : 0.0;
+    dst[idx] = d ? __dmul_rn(d[r], v) : v;
 }
 
+// iterate y (new order) -> x_perm(r) = y_r / a_rr in the caller's order
+// (IEEE division; d == nullptr: no scaling).
 __global__ void k_scatter_rows(const long long* __restrict__ perm, const double* __restrict__ src,
-                               double* __restrict__ dst, int n, int nrhs)
+                               const double* __restrict__ d, double* __restrict__ dst, int n, int nrhs)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n * nrhs) return;
     const int r = (int)(idx / nrhs), c = (int)(idx - (long long)r * nrhs);
-    dst[perm[r] * nrhs + c] = src[idx];
+    dst[perm[r] * nrhs + c] = d ? __ddiv_rn(src[idx], d[r]) : src[idx];
 }
 
-// c_r = b_perm(r) / a_rr  (IEEE division, as Algorithm 1's D^{-1} "computed once").
-__global__ void k_make_c(const long long* __restrict__ perm, const double* __restrict__ b,
-                         const double* __restrict__ d, double* __restrict__ c, int n)
+// The right-hand side in the new row order: b'_r = b_perm(r) (zero if b is NULL).
+__global__ void k_gather_b(const long long* __restrict__ perm, const double* __restrict__ b, double* __restrict__ out,
+                           int n)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    c[r] = b ? __ddiv_rn(b[perm[r]], d[r]) : 0.0;
+    out[r] = b ? b[perm[r]] : 0.0;
 }
 
 // ||b||_2 with a fixed reduction order (one CTA of 1024 threads).
@@ -1270,26 +1267,25 @@ cudaError_t launch_persistent(const void* fn, int grid, int threads, int smem, c
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-cudaError_t launch_gather_rows(const long long* perm, const double* src, double* dst, int n, int nrhs,
-                               cudaStream_t s)
+cudaError_t launch_gather_rows(const long long* perm, const double* src, const double* d, double* dst, int n,
+                               int nrhs, cudaStream_t s)
 {
     const long long tot = (long long)n * nrhs;
-    k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(perm, src, dst, n, nrhs);
+    k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(perm, src, d, dst, n, nrhs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_rows(const long long* perm, const double* src, double* dst, int n, int nrhs,
-                                cudaStream_t s)
+cudaError_t launch_scatter_rows(const long long* perm, const double* src, const double* d, double* dst, int n,
+                                int nrhs, cudaStream_t s)
 {
     const long long tot = (long long)n * nrhs;
-    k_scatter_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(perm, src, dst, n, nrhs);
+    k_scatter_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(perm, src, d, dst, n, nrhs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_make_c(const long long* perm, const double* b, const double* d, double* c, int n,
-                          JacCtl* ctl, cudaStream_t s)
+cudaError_t launch_gather_b(const long long* perm, const double* b, double* out, int n, JacCtl* ctl, cudaStream_t s)
 {
-    k_make_c<<<(n + 255) / 256, 256, 0, s>>>(perm, b, d, c, n);
+    k_gather_b<<<(n + 255) / 256, 256, 0, s>>>(perm, b, out, n);
     k_bnorm<<<1, 1024, 0, s>>>(b, n, ctl);
     return cudaGetLastError();
 }

@@ -19,12 +19,12 @@ int halo_smem_bytes(int rows, int emax, int xcap, int ntcap, int blkcap, int sta
 cudaError_t launch_persistent(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
                               const DevTiles& t, JacCtl* ctl, int max_sweeps, cudaStream_t s);
 
-cudaError_t launch_gather_rows(const long long* perm, const double* src, double* dst, int n, int nrhs,
-                               cudaStream_t s);
-cudaError_t launch_scatter_rows(const long long* perm, const double* src, double* dst, int n, int nrhs,
-                                cudaStream_t s);
-cudaError_t launch_make_c(const long long* perm, const double* b, const double* d, double* c, int n,
-                          JacCtl* ctl, cudaStream_t s);
+// x <-> iterate y = D x conversions (d == nullptr: plain permuted copy)
+cudaError_t launch_gather_rows(const long long* perm, const double* src, const double* d, double* dst, int n,
+                               int nrhs, cudaStream_t s);
+cudaError_t launch_scatter_rows(const long long* perm, const double* src, const double* d, double* dst, int n,
+                                int nrhs, cudaStream_t s);
+cudaError_t launch_gather_b(const long long* perm, const double* b, double* out, int n, JacCtl* ctl, cudaStream_t s);
 cudaError_t launch_arm(JacCtl* ctl, int test, int mixed, int inner, long long k_limit, long long k_delta,
                        double tol, int norm_kind, double* hist, long long hist_cap, long long timeout, int skip,
                        cudaStream_t s);
@@ -35,11 +35,12 @@ int batched_smem_bytes(int rows, int emax, int nrhs, int stages);
 int batched_threads(int rows);
 cudaError_t launch_batched(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
                            const DevTiles& t, const DevBatch& bt, JacCtl* ctl, int max_sweeps, cudaStream_t s);
-cudaError_t launch_batched_c(const double* b, const double* d, double* c, long long n, int nrhs, cudaStream_t s);
+cudaError_t launch_batched_scale(double* x, const double* d, long long n, int nrhs, cudaStream_t s);
 cudaError_t launch_batched_bnorm(const double* b, const long long* off, int nsys, int nrhs, double* bnorm,
                                  cudaStream_t s);
 cudaError_t launch_batched_gather_x(const double* x0, const double* x1, const int* row_sys, const int* mask,
-                                    const int* kpar, int cur, long long n, int nrhs, double* out, cudaStream_t s);
+                                    const int* kpar, int cur, long long n, int nrhs, const double* d, double* out,
+                                    cudaStream_t s);
 cudaError_t launch_batched_reset(const DevBatch& bt, int nrhs, cudaStream_t s);
 cudaError_t launch_adjoint_grad(const int* rowptr, const int* col, const double* lam, const double* x,
                                 double* dA, int n, cudaStream_t s);

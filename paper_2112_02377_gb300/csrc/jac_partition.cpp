@@ -174,10 +174,10 @@ Error make_plan(const HostCSR& A, jac_splitting s, int32_t nparts, const jac_opt
     return Error();
 }
 
-Error make_tform(const HostCSR& A, const Plan& plan, TForm& tf)
+Error make_scaled_form(const HostCSR& A, const Plan& plan, ScaledForm& tf)
 {
     const int64_t n = A.n;
-    tf = TForm();
+    tf = ScaledForm();
     tf.n = n;
     tf.rowptr.resize(n + 1);
     tf.d.resize(n);
@@ -200,15 +200,15 @@ Error make_tform(const HostCSR& A, const Plan& plan, TForm& tf)
     }
     const int64_t nnz_off = tf.rowptr[n];
     tf.col.resize(nnz_off);
-    tf.T.resize(nnz_off);
+    tf.S.resize(nnz_off);
     for (int64_t r = 0; r < n; ++r) {
         const int64_t i = plan.perm[r];
-        const double di = tf.d[r];
         int64_t w = tf.rowptr[r];
         for (int64_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
             if (A.col[k] == i) continue;
-            tf.col[w] = (int32_t)plan.iperm[A.col[k]];
-            tf.T[w] = -(A.val[k] / di);
+            const int64_t rj = plan.iperm[A.col[k]];
+            tf.col[w] = (int32_t)rj;
+            tf.S[w] = -(A.val[k] / tf.d[rj]);     // column scaling: -a_ij / a_jj
             ++w;
         }
     }
@@ -245,7 +245,7 @@ void dependency_lists(const HostCSR& A, const Plan& plan, std::vector<int64_t>& 
     }
 }
 
-void make_tiling(const TForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
+void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
                  int64_t ctas, Tiling& t)
 {
     t = Tiling();
@@ -288,7 +288,7 @@ void make_tiling(const TForm& tf, const Plan& plan, int32_t rows_per_tile, int32
     t.cta0[ctas] = (int32_t)nt;
 }
 
-void make_windows(const TForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w)
+void make_windows(const ScaledForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w)
 {
     const int64_t nt = t.ntiles();
     const int64_t GAP = 16;     // columns closer than this join one run
