@@ -101,9 +101,10 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _traffic_from_profile(kernel_src_hash: str):
+def _traffic_from_profile(kernel_src_hash: str, kernel: str):
     """Per-sweep DRAM bytes of the sweep kernel from the committed ncu summary,
-    or None if the summary is missing or was taken on a different kernel source."""
+    or None if the summary is missing or was taken on a different kernel source
+    or instantiation."""
     path = os.path.join(ROOT, "profiles", "sweep_fp64_laplace7.md")
     if not os.path.exists(path):
         return None
@@ -112,12 +113,25 @@ def _traffic_from_profile(kernel_src_hash: str):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != kernel_src_hash:
+    if vals.get("kernel_source_sha256_16") != kernel_src_hash or vals.get("kernel") != kernel:
         return None
     try:
         return float(vals["dram_bytes_per_sweep"])
     except (KeyError, ValueError):
         return None
+
+
+def _geometry(st) -> dict:
+    """Kernel instantiation a context runs, from its stats."""
+    v, rows, cps = st["variant"], st["tile_rows"], st["ctas_per_sm"]
+    if v == 2:
+        name = f"k_persistent<1,{3 if cps == 3 else 4},{'true' if st['precision'] == 1 else 'false'},{rows // 32}>"
+    elif v == 3:
+        name = "k_halo<3,false>"
+    else:
+        name = "k_row_sweep"
+    return {"kernel": name, "variant": v, "tile_rows": rows, "ctas_per_sm": cps, "ctas": st["ctas"],
+            "tiles": st["ntiles"]}
 
 
 def _kernel_hash() -> str:
@@ -194,6 +208,8 @@ def main():
                          "two warm-up launches then one more launch, no output line")
     ap.add_argument("--profile-precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--profile-variant", type=int, default=0, help="kernel variant of the profiling case (0 = default)")
+    ap.add_argument("--profile-rows", type=int, default=0, help="tile rows of the profiling case (0 = default)")
+    ap.add_argument("--profile-cps", type=int, default=0, help="CTAs per SM of the profiling case (0 = default)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -216,7 +232,8 @@ def main():
         K = args.profile_sweeps
         mixed = args.profile_precision == "mixed"
         o = J.opts(variant=args.profile_variant, sweeps_per_graph=K, device=local,
-                   precision=J.JAC_MIXED if mixed else J.JAC_FP64, inner_sweeps=max(2, K))
+                   precision=J.JAC_MIXED if mixed else J.JAC_FP64, inner_sweeps=max(2, K),
+                   tile_rows=args.profile_rows, ctas_per_sm=args.profile_cps)
         c = J.jac_setup(A, b, J.JAC_BANDROW, 64, o)
         if mixed:
             J.jac_solve(c, 0.0, 3 * K - 1)        # three launches of K sweeps (cycles of K)
@@ -231,7 +248,7 @@ def main():
     ctxs = []
     setup_s = []
     for split, P in SPLITS:
-        o = J.opts(sweeps_per_graph=K_PER_GRAPH, stream=stream.cuda_stream, device=local)
+        o = J.opts(sweeps_per_graph=K_PER_GRAPH, stream=stream.cuda_stream, device=local, autotune=1)
         if split == "substruct":
             o.grid[:] = [GRID] * 3
             o.subdomains[:] = list(SUBDOMAINS)
@@ -240,6 +257,7 @@ def main():
         setup_s.append(time.perf_counter() - t0)
     st0 = J.jac_stats(ctxs[0])
     assert abs(st0["bytes_per_sweep_fp64"] - bps) < 1, (st0["bytes_per_sweep_fp64"], bps)
+    geoms = [_geometry(J.jac_stats(c)) for c in ctxs]
 
     def step():
         ms = 0.0
@@ -281,7 +299,7 @@ def main():
     peak, peak_kind = _measured_peak()
     achieved = bps * sweeps / (kernel_ms * 1e-3) / 1e9
     khash = _kernel_hash()
-    traffic = _traffic_from_profile(khash)
+    traffic = _traffic_from_profile(khash, geoms[0]["kernel"])
 
     # ---------------- end to end through the C ABI with pinned host buffers
     xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
@@ -315,7 +333,7 @@ def main():
         ttr = {}
         xref = None
         for prec in ("fp64", "mixed"):
-            o = J.opts(sweeps_per_graph=256, stream=stream.cuda_stream, device=local,
+            o = J.opts(sweeps_per_graph=256, stream=stream.cuda_stream, device=local, autotune=1,
                        precision=J.JAC_MIXED if prec == "mixed" else J.JAC_FP64, inner_sweeps=MIXED_INNER)
             c = J.jac_setup(A, b, J.JAC_BANDROW, 64, o)
             k, rel, stt = J.jac_solve(c, TOL_TTR, 200000)
@@ -323,7 +341,7 @@ def main():
             x = J.jac_get_x(c)
             J.jac_free(c)
             ttr[prec] = {"seconds": round(st["last_ms"] / 1e3, 4), "sweeps": k, "relres": rel,
-                         "status": int(stt)}
+                         "status": int(stt), "kernel": _geometry(st)["kernel"]}
             if prec == "fp64":
                 xref = x
             else:
@@ -355,11 +373,13 @@ def main():
                        "sweeps_per_step": SWEEPS_PER_SPLIT * len(SPLITS), "sweeps_per_graph": K_PER_GRAPH,
                        "l2": "inputs larger than L2 (440.5 MB streamed per sweep), no flush",
                        "algorithmic_bytes_per_sweep": bps, "setup_seconds": [round(s, 3) for s in setup_s],
+                       "setup": "autotuned kernel geometry and CTA balance (jac_opts.autotune)",
+                       "geometry": geoms,
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "traffic": (traffic * K_PER_GRAPH if traffic is not None else None),
-                         "traffic_per_sweep": traffic, "kernel": "k_persistent<1,4,false,8>",
+                         "traffic_per_sweep": traffic, "kernel": sorted({g["kernel"] for g in geoms}),
                          "units_per_launch": K_PER_GRAPH, "bytes_per_unit": bps,
                          "frac_of_8TBs": round(achieved / 8000.0, 4)},
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

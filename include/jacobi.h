@@ -105,7 +105,9 @@ typedef struct {
     int32_t ctas_per_sm;       /* variant 2 with 256-row tiles: 0 = auto (2), or 3 (3-stage pipeline) */
     int32_t autotune;          /* 1: jac_setup / jac_setup_batched time a few sweeps of every kernel
                                   geometry (variant, tile_rows, ctas_per_sm) and keep the fastest;
-                                  needs variant = tile_rows = ctas_per_sm = 0 */
+                                  jac_setup then re-cuts the CTA row ranges from the measured per-CTA
+                                  compute times while that shortens the sweep.  Needs
+                                  variant = tile_rows = ctas_per_sm = 0 */
     int32_t history;           /* >0: record the relres of every evaluated iterate,
                                   up to this many entries (jac_get_history) */
     void* stream;              /* cudaStream_t for all work; NULL = legacy default stream */

@@ -46,6 +46,8 @@ struct jac_ctx {
     Partial* d_part = nullptr;
     int nslots = 0;
     unsigned long long* d_trace = nullptr;
+    std::vector<int32_t> h_cta_row0;      // ctas+1: first row of each CTA (persistent variants)
+    std::vector<double> h_row_cost;       // per-row cost estimates the CTA ranges were cut with
     JacCtl* d_ctl = nullptr;
     JacCtl* h_ctl = nullptr;     // pinned mirrors [2]
     double* d_hist = nullptr;
@@ -453,7 +455,7 @@ double time_per_sweep(jac_ctx* c)
         if ((st == JAC_OK || st == JAC_ENOTCONV) && k > 0) ms = c->last_ms / (double)k;
     } else {
         double rel = 0.0;
-        if (jac_sweep(c, 8, &rel) == JAC_OK && jac_sweep(c, 24, &rel) == JAC_OK) ms = c->last_ms / 24.0;
+        if (jac_sweep(c, 8, &rel) == JAC_OK && jac_sweep(c, 32, &rel) == JAC_OK) ms = c->last_ms / 32.0;
     }
     jac_set_x(c, nullptr, JAC_MEM_HOST);
     return ms;
@@ -540,49 +542,12 @@ jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t npart
     return JAC_OK;
 }
 
-jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, const jac_opts* o_in,
-                     jac_ctx** out)
+// One context with fixed options; row_cost (NULL: the default model) sets
+// how the persistent variants cut the CTA row ranges.
+static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, jac_opts o,
+                               const std::vector<double>* row_cost, jac_ctx** out)
 {
-    if (!out) return fail(nullptr, JAC_EINVAL, "out is NULL");
     *out = nullptr;
-    jac_opts o;
-    jac_opts_default(&o);
-    if (o_in) o = *o_in;
-    if (o.autotune) {
-        // Autotuner: set up every kernel geometry, time a few sweeps of each
-        // on this matrix, keep the fastest context.
-        if (o.variant || o.tile_rows || o.ctas_per_sm)
-            return fail(nullptr, JAC_EINVAL, "autotune needs variant = tile_rows = ctas_per_sm = 0");
-        const Geometry cand[] = {{2, 256, 2}, {2, 256, 3}, {2, 224, 0}, {2, 480, 0}, {3, 256, 0}};
-        jac_ctx* best = nullptr;
-        double best_ms = 1e30;
-        std::string first_err;
-        for (const Geometry& g : cand) {
-            jac_opts o2 = o;
-            o2.autotune = 0;
-            o2.variant = g.variant;
-            o2.tile_rows = g.rows;
-            o2.ctas_per_sm = g.ctas;
-            jac_ctx* c = nullptr;
-            const jac_status st = jac_setup(A, b, s, nparts, &o2, &c);
-            if (st != JAC_OK) {
-                if (first_err.empty()) first_err = g_setup_error;
-                if (st != JAC_EINVAL) return st;   // invalid matrix etc.: no geometry will do
-                continue;
-            }
-            const double ms = time_per_sweep(c);
-            if (ms < best_ms) {
-                if (best) jac_free(best);
-                best = c;
-                best_ms = ms;
-            } else {
-                jac_free(c);
-            }
-        }
-        if (!best) return fail(nullptr, JAC_EINVAL, "autotune: no kernel geometry could be set up: " + first_err);
-        *out = best;
-        return JAC_OK;
-    }
     if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
     jac_status st = check_opts(o, nullptr);
     if (st != JAC_OK) return st;
@@ -689,11 +654,10 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
         if (c->variant == 3) {
             // The tile table's size depends on the CTA count, which depends on
             // the shared memory per CTA: try 2 CTAs/SM, then 1.
-            make_tiling(tf, plan, rows, c->emax, 1, tl);
-            make_windows(tf, tl, c->xcap, c->maxruns, c->emax, win);
             for (int guess = 2; guess >= 1 && per_sm == 0; --guess) {
                 const int ctas = guess * prop.multiProcessorCount;
-                make_tiling(tf, plan, rows, c->emax, ctas, tl);
+                make_tiling(tf, plan, rows, c->emax, ctas, tl, row_cost);
+                make_windows(tf, tl, c->xcap, c->maxruns, c->emax, win);
                 int ntcap = 0, blkcap = 0;
                 for (int g = 0; g < ctas; ++g) {
                     ntcap = std::max(ntcap, tl.cta0[g + 1] - tl.cta0[g]);
@@ -730,8 +694,16 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
         c->grid = (int)((n + 255) / 256);
         c->emax = 0;
     }
-    if (c->variant == 2) make_tiling(tf, plan, c->rows_per_tile, c->emax, c->grid, tl);
-    if (c->variant >= 2) c->ntiles = (int)tl.ntiles();
+    if (c->variant == 2) make_tiling(tf, plan, c->rows_per_tile, c->emax, c->grid, tl, row_cost);
+    if (c->variant >= 2) {
+        c->ntiles = (int)tl.ntiles();
+        // what the balance calibration needs: each CTA's rows and the cost model used
+        c->h_cta_row0.resize(c->grid + 1);
+        for (int g = 0; g <= c->grid; ++g) c->h_cta_row0[g] = tl.row0[tl.cta0[g]];
+        c->h_row_cost.resize(n);
+        for (int64_t r = 0; r < n; ++r)
+            c->h_row_cost[r] = row_cost ? (*row_cost)[r] : default_row_cost(tf.rowptr[r + 1] - tf.rowptr[r]);
+    }
     c->nslots = c->grid;
 
     // ---- device buffers
@@ -814,6 +786,83 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     if (fetch_ctl(C, &c->h_ctl[0]) != JAC_OK) return fail(nullptr, JAC_ECUDA, C->err);
     CK(nullptr, sm ? cudaStreamSynchronize(sm) : cudaDeviceSynchronize());
     *out = c.release();
+    return JAC_OK;
+}
+
+
+jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, const jac_opts* o_in,
+                     jac_ctx** out)
+{
+    if (!out) return fail(nullptr, JAC_EINVAL, "out is NULL");
+    *out = nullptr;
+    jac_opts o;
+    jac_opts_default(&o);
+    if (o_in) o = *o_in;
+    if (!o.autotune) return setup_single(A, b, s, nparts, o, nullptr, out);
+    // Autotuner: set up every kernel geometry, time a few sweeps of each on
+    // this matrix and keep the fastest; then re-cut its CTA row ranges from
+    // the measured per-CTA compute times while that keeps paying.
+    if (o.variant || o.tile_rows || o.ctas_per_sm)
+        return fail(nullptr, JAC_EINVAL, "autotune needs variant = tile_rows = ctas_per_sm = 0");
+    const Geometry cand[] = {{2, 256, 2}, {2, 256, 3}, {2, 224, 0}, {2, 480, 0}, {3, 256, 0}};
+    jac_ctx* best = nullptr;
+    jac_opts best_o = o;
+    double best_ms = 1e30;
+    std::string first_err;
+    for (const Geometry& g : cand) {
+        jac_opts o2 = o;
+        o2.autotune = 0;
+        o2.variant = g.variant;
+        o2.tile_rows = g.rows;
+        o2.ctas_per_sm = g.ctas;
+        jac_ctx* c = nullptr;
+        const jac_status st = setup_single(A, b, s, nparts, o2, nullptr, &c);
+        if (st != JAC_OK) {
+            if (first_err.empty()) first_err = g_setup_error;
+            if (st != JAC_EINVAL) return st;   // invalid matrix etc.: no geometry will do
+            continue;
+        }
+        const double ms = time_per_sweep(c);
+        if (ms < best_ms) {
+            if (best) jac_free(best);
+            best = c;
+            best_o = o2;
+            best_ms = ms;
+        } else {
+            jac_free(c);
+        }
+    }
+    if (!best) return fail(nullptr, JAC_EINVAL, "autotune: no kernel geometry could be set up: " + first_err);
+    // Balance calibration: the sweep waits for the slowest CTA, so scale the
+    // cost estimate of every row by its CTA's measured time per unit of
+    // estimated cost and cut the ranges again.
+    for (int it = 0; it < 3 && best->variant >= 2 && best->n > 0; ++it) {
+        const int G = best->grid;
+        std::vector<double> comp(G, 0.0);
+        int64_t nct = 0;
+        if (jac_get_trace(best, comp.data(), nullptr, G, &nct) != JAC_OK || nct != G) break;
+        std::vector<double> w = best->h_row_cost;
+        for (int g = 0; g < G; ++g) {
+            const int64_t r0 = best->h_cta_row0[g], r1 = best->h_cta_row0[g + 1];
+            double W = 0.0;
+            for (int64_t r = r0; r < r1; ++r) W += w[r];
+            if (W <= 0.0 || !(comp[g] > 0.0)) continue;
+            const double f = comp[g] / W;
+            for (int64_t r = r0; r < r1; ++r) w[r] *= f;
+        }
+        jac_ctx* c = nullptr;
+        if (setup_single(A, b, s, nparts, best_o, &w, &c) != JAC_OK) break;
+        const double ms = time_per_sweep(c);
+        if (ms < best_ms) {
+            jac_free(best);
+            best = c;
+            best_ms = ms;
+        } else {
+            jac_free(c);
+            break;
+        }
+    }
+    *out = best;
     return JAC_OK;
 }
 

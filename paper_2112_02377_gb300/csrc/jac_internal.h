@@ -86,8 +86,10 @@ Error make_plan(const HostCSR& A, jac_splitting s, int32_t nparts, const jac_opt
 Error make_scaled_form(const HostCSR& A, const Plan& plan, ScaledForm& tf);
 void dependency_lists(const HostCSR& A, const Plan& plan, std::vector<int64_t>& recv_ptr,
                       std::vector<int32_t>& recv_from, std::vector<int64_t>& recv);
+// row_cost: per-row cost estimates in the new order (NULL: default_row_cost).
+double default_row_cost(int64_t off_entries);
 void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
-                 int64_t ctas, Tiling& t);
+                 int64_t ctas, Tiling& t, const std::vector<double>* row_cost = nullptr);
 HostCSR transpose_csr(const HostCSR& A);
 void make_windows(const ScaledForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w);
 

@@ -245,20 +245,54 @@ void dependency_lists(const HostCSR& A, const Plan& plan, std::vector<int64_t>& 
     }
 }
 
+double default_row_cost(int64_t off_entries)
+{
+    // Relative sweep cost of a row with `off_entries` off-diagonal entries:
+    // per-row work (row length, b, own y, store, residual) weighs about as
+    // much as six entries on GB300 (fitted to per-CTA times of the 160^3 sweep).
+    return 6.0 + (double)off_entries;
+}
+
 void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
-                 int64_t ctas, Tiling& t)
+                 int64_t ctas, Tiling& t, const std::vector<double>* row_cost)
 {
     t = Tiling();
     t.rows_per_tile = rows_per_tile;
     t.max_entries = max_entries;
+    const int64_t n = tf.n;
+    // CTA row ranges: contiguous, cut at row granularity so that every CTA
+    // carries the same estimated cost.
+    std::vector<double> pre(n + 1, 0.0);
+    for (int64_t r = 0; r < n; ++r) {
+        const double w = row_cost ? (*row_cost)[r] : default_row_cost(tf.rowptr[r + 1] - tf.rowptr[r]);
+        pre[r + 1] = pre[r] + w;
+    }
+    std::vector<int64_t> rb(ctas + 1, 0);
+    rb[ctas] = n;
+    {
+        int64_t cur = 0;
+        for (int64_t g = 1; g < ctas; ++g) {
+            const double target = pre[n] * (double)g / (double)ctas;
+            while (cur < n && pre[cur] + 0.5 * (pre[cur + 1] - pre[cur]) < target) ++cur;
+            rb[g] = cur;
+        }
+    }
+    // Tiles: at most rows_per_tile rows and max_entries staged entries, never
+    // crossing a partition or a CTA boundary.
     t.row0.push_back(0);
-    for (int64_t p = 0; p < plan.nparts(); ++p) {
-        int64_t r = plan.part_ptr[p];
-        const int64_t end = plan.part_ptr[p + 1];
+    t.cta0.assign(ctas + 1, 0);
+    int64_t p = 0;
+    const int64_t P = plan.nparts();
+    for (int64_t g = 0; g < ctas; ++g) {
+        t.cta0[g] = (int32_t)(t.row0.size() - 1);
+        int64_t r = rb[g];
+        const int64_t end = rb[g + 1];
         while (r < end) {
+            while (p + 1 < P && plan.part_ptr[p + 1] <= r) ++p;
+            const int64_t lim = std::min<int64_t>(end, plan.part_ptr[p + 1]);
             int64_t rows = 0, ent = 0;
-            while (r + rows < end && rows < rows_per_tile) {
-                int64_t len = tf.rowptr[r + rows + 1] - tf.rowptr[r + rows];
+            while (r + rows < lim && rows < rows_per_tile) {
+                const int64_t len = tf.rowptr[r + rows + 1] - tf.rowptr[r + rows];
                 if (rows > 0 && ent + len > max_entries) break;
                 ent += len;
                 ++rows;
@@ -270,22 +304,9 @@ void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, 
         }
     }
     const int64_t nt = t.ntiles();
+    t.cta0[ctas] = (int32_t)nt;
     t.nnz0.resize(nt + 1);
     for (int64_t i = 0; i <= nt; ++i) t.nnz0[i] = tf.rowptr[t.row0[i]];
-    // contiguous tile ranges per CTA, balanced by algorithmic bytes
-    std::vector<double> pre(nt + 1, 0.0);
-    for (int64_t i = 0; i < nt; ++i) {
-        double rows = t.row0[i + 1] - t.row0[i], ent = t.nnz0[i + 1] - t.nnz0[i];
-        pre[i + 1] = pre[i] + 12.0 * ent + 36.0 * rows;
-    }
-    t.cta0.assign(ctas + 1, 0);
-    int64_t cur = 0;
-    for (int64_t g = 1; g < ctas; ++g) {
-        const double target = pre[nt] * (double)g / (double)ctas;
-        while (cur < nt && pre[cur] + 0.5 * (pre[cur + 1] - pre[cur]) < target) ++cur;
-        t.cta0[g] = (int32_t)cur;
-    }
-    t.cta0[ctas] = (int32_t)nt;
 }
 
 void make_windows(const ScaledForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w)
