@@ -46,7 +46,7 @@ struct JacCtl {
 
 struct Partial {
     double ss;                // sum of r_i^2
-    unsigned long long mx;    // max |r_i| as IEEE bits (order-preserving for |r|)
+    unsigned long long mx;    // max over rows of abs_key(r_i)
 };
 
 // Off-diagonal iteration-matrix data in the new row order (constant during a
@@ -107,10 +107,22 @@ struct DevBatch {
     unsigned long long* pmx;    // [2][npairs][nrhs] partial max |r| (bits)
 };
 
-__device__ __forceinline__ unsigned long long abs_bits(double r)
+// Order key of |r|: the IEEE bits of r shifted left by one, which drops the
+// sign bit.  For finite r and +-Inf, key(a) < key(b) iff |a| < |b|, and NaN
+// keys lie above every finite and infinite one.  Built with integer shifts
+// only (a mask of the sign bit would be turned into an FP64 absolute value,
+// which takes a slot of the FP64 pipe in every row).
+__device__ __forceinline__ unsigned long long abs_key(double r)
 {
-    return (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
+    return (unsigned long long)__double_as_longlong(r) << 1;
 }
+
+__device__ __forceinline__ double abs_from_key(unsigned long long key)
+{
+    return __longlong_as_double((long long)(key >> 1));
+}
+
+constexpr unsigned long long KEY_INF = 0x7ff0000000000000ull << 1;   // key of +-Inf
 
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b)
 {
@@ -136,7 +148,7 @@ __device__ __forceinline__ void accumulate_residual(double ynew, double yold, do
 {
     const double r = __dadd_rn(ynew, -yold);
     ss = __fma_rn(r, r, ss);
-    mx = umax64(mx, abs_bits(r));
+    mx = umax64(mx, abs_key(r));
 }
 
 // Phase of a sweep: plain FP64 sweeps, or position `pos` in the mixed
@@ -180,9 +192,9 @@ __device__ __forceinline__ Decision decide(int test, double tol, long long k_lim
 {
     Decision d;
     d.res2 = sqrt(ss);
-    d.resinf = __longlong_as_double((long long)mx);
+    d.resinf = abs_from_key(mx);
     d.relres = (norm_kind == 2) ? (bnorm > 0.0 ? d.res2 / bnorm : d.res2) : d.resinf;
-    d.numeric_bad = !(ss <= 1.7976931348623157e308) || mx >= 0x7ff0000000000000ull;
+    d.numeric_bad = !(ss <= 1.7976931348623157e308) || mx >= KEY_INF;
     if (d.numeric_bad) d.done = DONE_NUMERIC;
     else if (test && d.relres <= tol) d.done = DONE_CONVERGED;
     else if (test && k >= k_limit) d.done = DONE_LIMIT;
