@@ -210,6 +210,10 @@ def main():
     ap.add_argument("--profile-variant", type=int, default=0, help="kernel variant of the profiling case (0 = default)")
     ap.add_argument("--profile-rows", type=int, default=0, help="tile rows of the profiling case (0 = default)")
     ap.add_argument("--profile-cps", type=int, default=0, help="CTAs per SM of the profiling case (0 = default)")
+    ap.add_argument("--pin-geometry", default="",
+                    help="ROWS:CTAS_PER_SM: set the contexts up with this kernel geometry and the default CTA "
+                         "balance instead of the autotuner (for ncu launch lists, whose serialised timing would "
+                         "steer the autotuner)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -248,7 +252,12 @@ def main():
     ctxs = []
     setup_s = []
     for split, P in SPLITS:
-        o = J.opts(sweeps_per_graph=K_PER_GRAPH, stream=stream.cuda_stream, device=local, autotune=1)
+        if args.pin_geometry:
+            rows_, cps_ = (int(v) for v in args.pin_geometry.split(":"))
+            o = J.opts(sweeps_per_graph=K_PER_GRAPH, stream=stream.cuda_stream, device=local, variant=2,
+                       tile_rows=rows_, ctas_per_sm=cps_)
+        else:
+            o = J.opts(sweeps_per_graph=K_PER_GRAPH, stream=stream.cuda_stream, device=local, autotune=1)
         if split == "substruct":
             o.grid[:] = [GRID] * 3
             o.subdomains[:] = list(SUBDOMAINS)
@@ -333,7 +342,8 @@ def main():
         ttr = {}
         xref = None
         for prec in ("fp64", "mixed"):
-            o = J.opts(sweeps_per_graph=256, stream=stream.cuda_stream, device=local, autotune=1,
+            o = J.opts(sweeps_per_graph=256, stream=stream.cuda_stream, device=local,
+                       autotune=0 if args.pin_geometry else 1,
                        precision=J.JAC_MIXED if prec == "mixed" else J.JAC_FP64, inner_sweeps=MIXED_INNER)
             c = J.jac_setup(A, b, J.JAC_BANDROW, 64, o)
             k, rel, stt = J.jac_solve(c, TOL_TTR, 200000)
@@ -373,7 +383,8 @@ def main():
                        "sweeps_per_step": SWEEPS_PER_SPLIT * len(SPLITS), "sweeps_per_graph": K_PER_GRAPH,
                        "l2": "inputs larger than L2 (440.5 MB streamed per sweep), no flush",
                        "algorithmic_bytes_per_sweep": bps, "setup_seconds": [round(s, 3) for s in setup_s],
-                       "setup": "autotuned kernel geometry and CTA balance (jac_opts.autotune)",
+                       "setup": ("pinned geometry " + args.pin_geometry) if args.pin_geometry else
+                                "autotuned kernel geometry and CTA balance (jac_opts.autotune)",
                        "geometry": geoms,
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
