@@ -126,13 +126,14 @@ def _geometry(st) -> dict:
     """Kernel instantiation a context runs, from its stats."""
     v, rows, cps = st["variant"], st["tile_rows"], st["ctas_per_sm"]
     if v == 2:
-        name = f"k_persistent<1,{3 if cps == 3 else 4},{'true' if st['precision'] == 1 else 'false'},{rows // 32}>"
+        name = (f"k_persistent<1,{3 if cps == 3 else 4},{'true' if st['precision'] == 1 else 'false'},"
+                f"{rows // 32},{st['lanes_per_row']}>")
     elif v == 3:
         name = "k_halo<3,false>"
     else:
         name = "k_row_sweep"
-    return {"kernel": name, "variant": v, "tile_rows": rows, "ctas_per_sm": cps, "ctas": st["ctas"],
-            "tiles": st["ntiles"]}
+    return {"kernel": name, "variant": v, "tile_rows": rows, "ctas_per_sm": cps,
+            "lanes_per_row": st["lanes_per_row"], "ctas": st["ctas"], "tiles": st["ntiles"]}
 
 
 def _kernel_hash() -> str:

@@ -100,9 +100,15 @@ typedef struct {
                                   2 = persistent grid-synchronised pipelined kernel, x gathered
                                   from L2; 3 = as 2 with each tile's x halo (its dependency list,
                                   Sec. 4.2.2) staged into shared memory */
-    int32_t tile_rows;         /* rows per tile: 0 = auto (256 FP64, 480 mixed), 224, 256 or 480
-                                  (variant 2); 256 (variant 3) */
+    int32_t tile_rows;         /* threads of a tile (one row each when lanes_per_row = 1): 0 = auto
+                                  (256), 224, 256 or 480 (variant 2); 256 (variant 3) */
     int32_t ctas_per_sm;       /* variant 2 with 256-row tiles: 0 = auto (2), or 3 (3-stage pipeline) */
+    int32_t lanes_per_row;     /* variant 2 with 256-thread tiles: lanes summing one row (1, 2, 4, 8);
+                                  0 = auto: the smallest count whose tile of 256/L longest rows fits a
+                                  pipeline stage.  Each row is summed by L interleaved FMA chains and
+                                  a fixed pairwise tree, so iterates are bit-identical across
+                                  splittings and tilings for a given L and agree to rounding
+                                  across L. */
     int32_t autotune;          /* 1: jac_setup / jac_setup_batched time a few sweeps of every kernel
                                   geometry (variant, tile_rows, ctas_per_sm) and keep the fastest;
                                   jac_setup then re-cuts the CTA row ranges from the measured per-CTA
@@ -138,6 +144,7 @@ typedef struct {
     double bytes_per_sweep_fp32;  /* algorithmic HBM bytes of one FP32 inner sweep */
     int32_t variant, precision, splitting, nrhs;
     int32_t tile_rows, ctas_per_sm;  /* kernel geometry in use (chosen by the autotuner if enabled) */
+    int32_t lanes_per_row;           /* lanes per row in use (a tile holds tile_rows / lanes_per_row rows) */
 } jac_stats_t;
 
 /* Defaults for every option. */

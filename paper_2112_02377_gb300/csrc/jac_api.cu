@@ -69,6 +69,7 @@ struct jac_ctx {
     int64_t fallback_tiles = 0, window_elems = 0;
     int sms = 1;
     int ntiles = 0, emax = 0, rows_per_tile = 256, stages = 4, grid = 0, threads = 0, smem = 0;
+    int lanes = 1;                        // lanes per row (persistent variant, 256 threads)
     const void* pfn64 = nullptr;
     const void* pfnmix = nullptr;
     int K = 64;
@@ -434,6 +435,9 @@ jac_status check_opts(const jac_opts& o, jac_ctx* err_ctx)
     if (o.history < 0) return fail(err_ctx, JAC_EINVAL, "opts.history must be >= 0");
     if (o.ctas_per_sm != 0 && o.ctas_per_sm != 2 && o.ctas_per_sm != 3)
         return fail(err_ctx, JAC_EINVAL, "opts.ctas_per_sm must be 0, 2 or 3");
+    if (o.lanes_per_row != 0 && o.lanes_per_row != 1 && o.lanes_per_row != 2 && o.lanes_per_row != 4 &&
+        o.lanes_per_row != 8)
+        return fail(err_ctx, JAC_EINVAL, "opts.lanes_per_row must be 0, 1, 2, 4 or 8");
     return JAC_OK;
 }
 
@@ -462,7 +466,7 @@ double time_per_sweep(jac_ctx* c)
 }
 
 struct Geometry {
-    int variant, rows, ctas;
+    int variant, rows, ctas, lanes;   // lanes 0: automatic
 };
 
 }  // namespace
@@ -542,6 +546,8 @@ jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t npart
     return JAC_OK;
 }
 
+inline int64_t nnz_off_of(const ScaledForm& tf) { return tf.rowptr.empty() ? 0 : tf.rowptr.back(); }
+
 // One context with fixed options; row_cost (NULL: the default model) sets
 // how the persistent variants cut the CTA row ranges.
 static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, jac_opts o,
@@ -598,18 +604,31 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     CK(nullptr, cudaGetDeviceProperties(&prop, dev));
     Tiling tl;
     Windows win;
-    // Defaults (measured at 160^3 on GB300): FP64 sweeps are bound by the FP64
-    // pipe and run best with the plain loop, 8 math warps x 2 CTAs/SM; the FP32
-    // inner sweeps of the mixed solve are latency bound and run best with the
-    // software-pipelined loop, 15 math warps x 1 CTA/SM.
+    // Default geometry: the persistent kernel with 8 math warps (256 threads),
+    // 2 CTAs/SM and the plain row loop; the autotuner also tries 3 CTAs/SM
+    // and the 7/15-warp software-pipelined geometries.
     c->variant = o.variant == 0 ? 2 : o.variant;
-    c->rows_per_tile = o.tile_rows ? o.tile_rows : (o.precision == JAC_MIXED && c->variant == 2 ? 480 : 256);
+    c->rows_per_tile = o.tile_rows ? o.tile_rows : 256;
     c->stages = 4;
     if (c->variant == 3 && c->rows_per_tile != 256) c->variant = 2;
     const int target_per_sm = (c->variant == 2 && c->rows_per_tile == 256 && o.ctas_per_sm == 3) ? 3 : 2;
     if (target_per_sm == 3) c->stages = 3;
+    // Lanes per row (256-thread geometry only): long rows fill a stage's
+    // entry budget with few rows, which leaves math warps without a row, and
+    // a long FMA chain per thread; L lanes per row split both.  Each lane's
+    // extra cost is the group's shuffle tree.  Auto: halve the entries per
+    // lane while at least 8 remain (measured on GB300: 26-entry FE rows run
+    // best with L = 2, 7-point rows with L = 1).
+    c->lanes = 1;
+    if (c->variant == 2 && c->rows_per_tile == 256) {
+        const double avg = n > 0 ? (double)nnz_off_of(tf) / (double)n : 0.0;
+        if (o.lanes_per_row) c->lanes = o.lanes_per_row;
+        else while (c->lanes < 8 && avg / (2.0 * c->lanes) >= 8.0) c->lanes *= 2;
+    } else if (o.lanes_per_row > 1) {
+        return fail(nullptr, JAC_EINVAL, "opts.lanes_per_row > 1 needs variant 2 with 256-thread tiles");
+    }
     if (c->variant >= 2) {
-        const int rows = c->rows_per_tile;
+        const int rows = c->rows_per_tile / c->lanes;     // rows of a tile
         int64_t cap_entries = (int64_t)std::max<int64_t>(1, tf.max_off) * rows;
         int64_t stage_budget;
         if (c->variant == 3) {
@@ -628,11 +647,11 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
             c->pfn64 = halo_kernel(c->stages, false);
             c->pfnmix = halo_kernel(c->stages, true);
         } else {
-            c->pfn64 = persistent_kernel(rows, c->stages, false);
-            c->pfnmix = persistent_kernel(rows, c->stages, true);
+            c->pfn64 = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes);
+            c->pfnmix = persistent_kernel(c->rows_per_tile, c->stages, true, c->lanes);
             c->smem = persistent_smem_bytes(rows, c->emax, c->stages);
         }
-        c->threads = (c->variant == 3) ? 256 + 32 : persistent_threads(rows);
+        c->threads = (c->variant == 3) ? 256 + 32 : persistent_threads(c->rows_per_tile);
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         auto occupancy = [&](int smem_bytes) -> int {
@@ -694,7 +713,7 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
         c->grid = (int)((n + 255) / 256);
         c->emax = 0;
     }
-    if (c->variant == 2) make_tiling(tf, plan, c->rows_per_tile, c->emax, c->grid, tl, row_cost);
+    if (c->variant == 2) make_tiling(tf, plan, c->rows_per_tile / c->lanes, c->emax, c->grid, tl, row_cost);
     if (c->variant >= 2) {
         c->ntiles = (int)tl.ntiles();
         // what the balance calibration needs: each CTA's rows and the cost model used
@@ -804,7 +823,24 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     // the measured per-CTA compute times while that keeps paying.
     if (o.variant || o.tile_rows || o.ctas_per_sm)
         return fail(nullptr, JAC_EINVAL, "autotune needs variant = tile_rows = ctas_per_sm = 0");
-    const Geometry cand[] = {{2, 256, 2}, {2, 256, 3}, {2, 224, 0}, {2, 480, 0}, {3, 256, 0}};
+    std::vector<Geometry> cand = {{2, 256, 2, 0}, {2, 256, 3, 0}, {2, 224, 0, 0}, {2, 480, 0, 0}, {3, 256, 0, 0}};
+    if (o.lanes_per_row == 0) {
+        // the lane counts next to the automatic one (its own arithmetic: see jac_opts.lanes_per_row)
+        jac_ctx* probe = nullptr;
+        jac_opts op = o;
+        op.autotune = 0;
+        op.variant = 2;
+        op.tile_rows = 256;
+        if (setup_single(A, b, s, nparts, op, nullptr, &probe) == JAC_OK) {
+            const int la = probe->lanes;
+            jac_free(probe);
+            for (int L : {la / 2, la * 2})
+                if (L >= 1 && L <= 8) {
+                    cand.push_back({2, 256, 2, L});
+                    cand.push_back({2, 256, 3, L});
+                }
+        }
+    }
     jac_ctx* best = nullptr;
     jac_opts best_o = o;
     double best_ms = 1e30;
@@ -815,6 +851,7 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
         o2.variant = g.variant;
         o2.tile_rows = g.rows;
         o2.ctas_per_sm = g.ctas;
+        if (g.lanes) o2.lanes_per_row = g.lanes;
         jac_ctx* c = nullptr;
         const jac_status st = setup_single(A, b, s, nparts, o2, nullptr, &c);
         if (st != JAC_OK) {
@@ -908,6 +945,7 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
         jac_opts chk = o;
         chk.nrhs = 1;
         chk.tile_rows = 0;
+        chk.lanes_per_row = 0;
         jac_status st = check_opts(chk, nullptr);
         if (st != JAC_OK) return st;
     }
@@ -1435,6 +1473,7 @@ jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
     out->splitting = c->splitting;
     out->nrhs = c->nrhs;
     out->tile_rows = c->variant >= 2 ? c->rows_per_tile : 0;
+    out->lanes_per_row = c->variant >= 2 ? c->lanes : 1;
     out->ctas_per_sm = (c->variant >= 2 && c->n > 0 && c->grid > 0) ? c->grid / std::max(1, c->sms) : 0;
     return JAC_OK;
 }

@@ -76,6 +76,58 @@ __device__ __forceinline__ void rows_dot(Real (&acc)[RPT], const int (&kb)[RPT],
     }
 }
 
+// A row summed by a group of L consecutive lanes (long rows): lane q of the
+// group runs one FMA chain over the row's entries q, q+L, q+2L, ... in stored
+// order, starting from `acc` (the caller passes b_i to lane 0 and 0 to the
+// others); group_sum then adds the L chains with a fixed xor-shuffle tree.  The
+// result depends only on the row and L, never on the tiling or the splitting.
+// The loop stops at the warp's longest per-lane count (a warp-uniform bound).
+template <int L, class Real, class LdT, class LdX>
+__device__ __forceinline__ Real lanes_dot(Real acc, int kb, int len, int q, LdT ldt, LdX ldx)
+{
+    const int my = len > q ? (len - q + L - 1) / L : 0;
+    const int lmax = (int)__reduce_max_sync(__activemask(), (unsigned)my);
+    for (int o = 0; o < lmax; o += CHUNK) {
+        Real xv[CHUNK];
+#pragma unroll
+        for (int u = 0; u < CHUNK; ++u)
+            if (o + u < my) xv[u] = ldx(kb + q + (o + u) * L);
+#pragma unroll
+        for (int u = 0; u < CHUNK; ++u) {
+            if (o + u >= lmax) break;
+            if (o + u < my) {
+                if constexpr (sizeof(Real) == 8) acc = __fma_rn(ldt(kb + q + (o + u) * L), xv[u], acc);
+                else acc = __fmaf_rn(ldt(kb + q + (o + u) * L), xv[u], acc);
+            }
+        }
+    }
+    return acc;
+}
+
+// Sum over the L lanes of a group (all lanes of the warp must call it); every
+// lane of the group gets the same value (the adds are commutative pairwise).
+template <int L, class Real>
+__device__ __forceinline__ Real group_sum(Real v)
+{
+#pragma unroll
+    for (int off = L / 2; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// A row of an oversized tile (its S and col were not staged), summed by L
+// lanes straight from global memory; kept out of line so that the staged
+// loop's register allocation does not carry it.
+template <int L, class Real>
+__device__ __noinline__ Real lanes_global(const Real* S, const int* col, const Real* src, int kb, int len, int q,
+                                          Real acc)
+{
+    for (int e = kb + q; e < kb + len; e += L) {
+        if constexpr (sizeof(Real) == 8) acc = __fma_rn(__ldg(S + e), __ldcg(src + __ldg(col + e)), acc);
+        else acc = __fmaf_rn(__ldg(S + e), __ldcg(src + __ldg(col + e)), acc);
+    }
+    return acc;
+}
+
 // Entries prefetched per row by the pipelined persistent kernel (a 7-point row
 // has 6 off-diagonal entries); longer rows finish in row_tail.
 constexpr int PF = 6;
@@ -270,16 +322,18 @@ __device__ __forceinline__ void consumer_sync()
 // Register budget: each SM sub-partition holds 16K registers and a CTA's warps
 // are dealt round-robin to the 4 sub-partitions, so (math warps + producer)
 // in multiples of 4 per SM leave 128 registers a thread; 2 x 9 warps leave 96.
-template <int RPT, int STAGES, bool MIXED, int NWM>
+// LPR = lanes per row: a tile holds 256/LPR rows, each summed by LPR lanes.
+template <int RPT, int STAGES, bool MIXED, int NWM, int LPR>
 __global__ void __maxnreg__(NWM == 8 ? (STAGES == 3 ? 72 : 96) : 128)
 k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int CT = NWM * 32, NW = NWM, ROWS = CT * RPT;
+    constexpr int CT = NWM * 32, NW = NWM, ROWS = CT * RPT / LPR;
     // 7 or 15 math warps have 128 registers: software-pipeline the x gathers of
     // the next tile (pays off when latency, not the FP64 pipe, bounds the sweep:
     // the FP32 inner sweeps); 8 math warps (96 registers) use the plain loop.
     constexpr bool PIPE = (NWM != 8);
+    static_assert(!PIPE || LPR == 1, "the pipelined loop sums a row in one lane");
     const StageLayout L = stage_layout(ROWS, t.emax);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes);
     uint64_t* empty = full + STAGES;
@@ -531,41 +585,45 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                     const bool over = (p1 - p0) > emax;
                     const int* srp = reinterpret_cast<const int*>(st + L.o_rp) - (r0 & ~3);
                     const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (p0 & ~3);
-                    const int r = r0 + tid;
+                    const int q = tid % LPR;              // lane within the row's group
+                    const int r = r0 + tid / LPR;
                     const bool in = r < r1;
-                    const int kb1[1] = {in ? srp[r] : 0};
-                    const int len1[1] = {in ? srp[r + 1] - kb1[0] : 0};
+                    const bool lead = in && q == 0;       // the lane that owns the row's result
+                    const int kb = in ? srp[r] : 0;
+                    const int len = in ? srp[r + 1] - kb : 0;
                     if (norm_ph) {
                         const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
                         const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
-                        const double xi = in ? __ldcg(xs + r) : 0.0;
-                        double a1[1] = {in ? sc[r] : 0.0};
+                        const double xi = lead ? __ldcg(xs + r) : 0.0;
+                        double acc = lead ? sc[r] : 0.0;
                         if (!over)
-                            rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
-                                        [&](int e) { return __ldcg(xs + scol[e]); });
+                            acc = lanes_dot<LPR>(acc, kb, len, q, [&](int e) { return sv[e]; },
+                                                 [&](int e) { return __ldcg(xs + scol[e]); });
                         else if (in)
-                            a1[0] = row_global(m.S64, m.col, xs, kb1[0], len1[0], a1[0]);
-                        if (in) {
+                            acc = lanes_global<LPR>(m.S64, m.col, xs, kb, len, q, acc);
+                        acc = group_sum<LPR>(acc);
+                        if (lead) {
                             if (ph == PH_P64) {
-                                __stcg(xd + r, a1[0]);
+                                __stcg(xd + r, acc);
                             } else {
-                                const float dl = (float)__dadd_rn(a1[0], -xi);
+                                const float dl = (float)__dadd_rn(acc, -xi);
                                 __stcg(v.dlt + r, dl);
                                 __stcg(v.e[1] + r, dl);
                             }
-                            accumulate_residual(a1[0], xi, ss, mx);
+                            accumulate_residual(acc, xi, ss, mx);
                         }
                     } else {
                         const float* sv = reinterpret_cast<const float*>(st + L.o_val) - (p0 & ~3);
-                        float a1[1] = {in ? __ldcg(v.dlt + r) : 0.f};
+                        float acc = lead ? __ldcg(v.dlt + r) : 0.f;
                         if (!over)
-                            rows_dot<1>(a1, kb1, len1, [&](int e) { return sv[e]; },
-                                        [&](int e) { return __ldcg(es + scol[e]); });
+                            acc = lanes_dot<LPR>(acc, kb, len, q, [&](int e) { return sv[e]; },
+                                                 [&](int e) { return __ldcg(es + scol[e]); });
                         else if (in)
-                            a1[0] = row_global(m.S32, m.col, es, kb1[0], len1[0], a1[0]);
-                        if (in) {
-                            if (ph == PH_P32) __stcg(ed + r, a1[0]);
-                            else __stcg(v.x[xb] + r, __dadd_rn(__ldcg(v.x[xb] + r), (double)a1[0]));
+                            acc = lanes_global<LPR>(m.S32, m.col, es, kb, len, q, acc);
+                        acc = group_sum<LPR>(acc);
+                        if (lead) {
+                            if (ph == PH_P32) __stcg(ed + r, acc);
+                            else __stcg(v.x[xb] + r, __dadd_rn(__ldcg(v.x[xb] + r), (double)acc));
                         }
                     }
                 }
@@ -1229,22 +1287,37 @@ cudaError_t launch_row_sweep(int ph, const DevMat& m, const DevVec& v, JacCtl* c
     return cudaGetLastError();
 }
 
-template <int RPT, int STAGES, bool MIXED, int NWM>
+template <int RPT, int STAGES, bool MIXED, int NWM, int LPR = 1>
 static const void* persistent_fn()
 {
-    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED, NWM>);
+    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED, NWM, LPR>);
 }
 
-// rows = rows per tile = 32 x math warps: 224 -> 7 (2 CTAs/SM, 128 regs),
-// 256 -> 8 (2 CTAs/SM, 96 regs; or 3 stages, 72 regs, 3 CTAs/SM),
-// 480 -> 15 (1 CTA/SM, 128 regs).
-const void* persistent_kernel(int rows, int stages, bool mixed)
+template <int STAGES, bool MIXED>
+static const void* persistent_fn_lanes(int lanes)
 {
-    if (rows == 256 && stages == 3) return mixed ? persistent_fn<1, 3, true, 8>() : persistent_fn<1, 3, false, 8>();
+    switch (lanes) {
+    case 1: return persistent_fn<1, STAGES, MIXED, 8, 1>();
+    case 2: return persistent_fn<1, STAGES, MIXED, 8, 2>();
+    case 4: return persistent_fn<1, STAGES, MIXED, 8, 4>();
+    case 8: return persistent_fn<1, STAGES, MIXED, 8, 8>();
+    default: return nullptr;
+    }
+}
+
+// threads = 32 x math warps: 224 -> 7 (2 CTAs/SM, 128 regs),
+// 256 -> 8 (2 CTAs/SM, 96 regs; or 3 stages, 72 regs, 3 CTAs/SM),
+// 480 -> 15 (1 CTA/SM, 128 regs).  lanes = lanes per row (256 threads only);
+// a tile then holds threads / lanes rows.
+const void* persistent_kernel(int threads, int stages, bool mixed, int lanes)
+{
+    if (threads == 256 && stages == 3)
+        return mixed ? persistent_fn_lanes<3, true>(lanes) : persistent_fn_lanes<3, false>(lanes);
     if (stages != 4) return nullptr;
-    if (rows == 224) return mixed ? persistent_fn<1, 4, true, 7>() : persistent_fn<1, 4, false, 7>();
-    if (rows == 256) return mixed ? persistent_fn<1, 4, true, 8>() : persistent_fn<1, 4, false, 8>();
-    if (rows == 480) return mixed ? persistent_fn<1, 4, true, 15>() : persistent_fn<1, 4, false, 15>();
+    if (threads == 256) return mixed ? persistent_fn_lanes<4, true>(lanes) : persistent_fn_lanes<4, false>(lanes);
+    if (lanes != 1) return nullptr;
+    if (threads == 224) return mixed ? persistent_fn<1, 4, true, 7>() : persistent_fn<1, 4, false, 7>();
+    if (threads == 480) return mixed ? persistent_fn<1, 4, true, 15>() : persistent_fn<1, 4, false, 15>();
     return nullptr;
 }
 

@@ -98,20 +98,77 @@ def test_per_sweep_parity_and_splitting_invariance(name, A, b, variant):
 
 
 @pytest.mark.parametrize("name,A,b", list(_cases())[:2])
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_lanes_per_row_parity_and_splitting_invariance(name, A, b, lanes):
+    """Rows summed by 2, 4 or 8 lanes: per-sweep parity with the oracle, and
+    the same bits under every splitting and tile balance for a given count."""
+    rng = np.random.default_rng(3)
+    x0 = rng.uniform(-1, 1, A.n)
+    Mo = O.prepare(A)
+    finals = []
+    for split, P in SPLITS:
+        for cps in (2, 3):
+            ctx = _setup(A, b, split, P, variant=2, lanes_per_row=lanes, ctas_per_sm=cps, sweeps_per_graph=7)
+            try:
+                assert J.jac_stats(ctx)["lanes_per_row"] == lanes
+                J.jac_set_x(ctx, x0)
+                x = x0.copy()
+                for k in range(3):
+                    rel = J.jac_sweep(ctx, 1)
+                    xg = J.jac_get_x(ctx)
+                    y, ss, mx = O.sweep(Mo, b, x)
+                    _assert_sweep_close(A, b, x, xg, y)
+                    assert abs(rel - np.sqrt(ss) / np.linalg.norm(b)) <= _relres_tol(A, b, x)
+                    x = xg
+                J.jac_sweep(ctx, 30)
+                finals.append(J.jac_get_x(ctx))
+            finally:
+                J.jac_free(ctx)
+    for f in finals[1:]:
+        assert np.array_equal(f, finals[0])
+
+
+def test_lanes_per_row_auto_choice_and_mixed():
+    A = W.fe27_deleted(14, seed=3)
+    xs, b = W.solution_and_rhs(A, 1)
+    avg = (A.nnz - A.n) / A.n                    # off-diagonal entries per row
+    want = 1
+    while want < 8 and avg / (2 * want) >= 8:    # halve the entries per lane while >= 8 remain
+        want *= 2
+    assert want == 2
+    ctx = _setup(A, b, "bandrow_nnz", 4, variant=2)
+    try:
+        assert J.jac_stats(ctx)["lanes_per_row"] == want
+    finally:
+        J.jac_free(ctx)
+    ctx = _setup(A, b, "bandrow_nnz", 4, variant=2, precision=J.JAC_MIXED, inner_sweeps=32, lanes_per_row=4)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-10, 20000)
+        assert st == J.JAC_OK
+        x = J.jac_get_x(ctx)
+        assert np.linalg.norm(b - O.spmv(A, x)) / np.linalg.norm(b) <= 1e-10
+    finally:
+        J.jac_free(ctx)
+    with pytest.raises(J.JacobiError):
+        _setup(A, b, "bandrow", 4, variant=2, tile_rows=480, lanes_per_row=2)
+
+
+@pytest.mark.parametrize("name,A,b", list(_cases())[:2])
 def test_variants_and_graph_batching_are_bit_identical(name, A, b):
     outs = []
     for variant, K, rows, cps in [(1, 64, 256, 0), (2, 64, 256, 0), (2, 7, 256, 0), (2, 1, 256, 0),
                                   (2, 64, 256, 3), (2, 64, 480, 0), (2, 5, 480, 0), (2, 64, 224, 0),
                                   (3, 64, 256, 0), (3, 3, 256, 0), (3, 1, 256, 0), (0, 9, 0, 0)]:
+        # one lane per row everywhere: the arithmetic the row and halo kernels share
         kw = dict(autotune=1) if variant == 0 else dict(variant=variant, tile_rows=rows, ctas_per_sm=cps)
-        ctx = _setup(A, b, "bandrow", 3, sweeps_per_graph=K, **kw)
+        ctx = _setup(A, b, "bandrow", 3, sweeps_per_graph=K, lanes_per_row=1, **kw)
         try:
             J.jac_sweep(ctx, 23)
             J.jac_sweep(ctx, 14)
             outs.append(J.jac_get_x(ctx))
         finally:
             J.jac_free(ctx)
-    ctx = _setup(A, b, "bandrow", 3, variant=2)
+    ctx = _setup(A, b, "bandrow", 3, variant=2, lanes_per_row=1)
     try:
         for _ in range(37):
             J.jac_sweep(ctx, 1)
