@@ -262,11 +262,19 @@ def run_extra(args, local, stream):
     # ---- adjoint, 96^3 variable-coefficient diffusion
     import torch
     from paper_2112_02377_gb300.autograd import jacobi_solve
+    dev = torch.device("cuda", local)
+    # warm-up on a small system: PyTorch's first backward pass loads (or
+    # JIT-compiles) its own elementwise kernels, which is not the solver's time
+    Aw = W.diffusion7(8, seed=1)
+    vw = torch.tensor(Aw.val, device=dev, requires_grad=True)
+    bw = torch.ones(Aw.n, dtype=torch.float64, device=dev, requires_grad=True)
+    xw = jacobi_solve(torch.tensor(Aw.rowptr, device=dev), torch.tensor(Aw.col, device=dev), vw, bw, tol=1e-10)
+    (0.5 * torch.sum(xw ** 2)).backward()
+    torch.cuda.synchronize()
     A = W.diffusion7(96, seed=5)
     rng = np.random.default_rng(7)
     bh = rng.uniform(-1, 1, A.n)
-    xt = torch.tensor(rng.uniform(-1, 1, A.n), device="cuda")
-    dev = torch.device("cuda", local)
+    xt = torch.tensor(rng.uniform(-1, 1, A.n), device=dev)
     rp = torch.tensor(A.rowptr, device=dev)
     cl = torch.tensor(A.col, device=dev)
     val = torch.tensor(A.val, device=dev, requires_grad=True)
