@@ -67,6 +67,16 @@ typedef enum {
                              ||D(x^{k+1} - x^k)||_inf, which equals it) */
 } jac_norm;
 
+/* How the persistent kernel orders consecutive sweeps (jac_opts.sync). */
+typedef enum {
+    JAC_SYNC_GRID = 0,       /* a grid-wide barrier after every sweep, then the test of that sweep */
+    JAC_SYNC_NEIGHBOUR = 1   /* FP64 sweeps (variant 2, 256 threads): a CTA waits only for the CTAs
+                                that own the rows it reads (its dependency list, Sec. 4.2.2) and for
+                                the residual sums of the sweep before last; the test of x^k is taken
+                                one sweep later and x^k is kept for it, so results and counts are
+                                those of JAC_SYNC_GRID */
+} jac_sync;
+
 /* Square sparse matrix in CSR form (Sec. 4.1: AA = val, JA = col, IA = rowptr).
  * rowptr has n+1 entries, rowptr[0] == index_base, rowptr[n] == nnz + index_base;
  * col/val have nnz entries; index_base is 0 or 1 (the paper prints 1-based
@@ -109,6 +119,7 @@ typedef struct {
                                   a fixed pairwise tree, so iterates are bit-identical across
                                   splittings and tilings for a given L and agree to rounding
                                   across L. */
+    int32_t sync;              /* jac_sync (default JAC_SYNC_GRID; the autotuner tries both) */
     int32_t autotune;          /* 1: jac_setup / jac_setup_batched time a few sweeps of every kernel
                                   geometry (variant, tile_rows, ctas_per_sm) and keep the fastest;
                                   jac_setup then re-cuts the CTA row ranges from the measured per-CTA
@@ -145,6 +156,7 @@ typedef struct {
     int32_t variant, precision, splitting, nrhs;
     int32_t tile_rows, ctas_per_sm;  /* kernel geometry in use (chosen by the autotuner if enabled) */
     int32_t lanes_per_row;           /* lanes per row in use (a tile holds tile_rows / lanes_per_row rows) */
+    int32_t sync;                    /* jac_sync in use for FP64 sweeps */
 } jac_stats_t;
 
 /* Defaults for every option. */

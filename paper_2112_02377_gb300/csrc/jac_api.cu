@@ -40,7 +40,13 @@ struct jac_ctx {
     float* d_S32 = nullptr;
     double* d_b = nullptr;         // b in the new row order (FP64 sweep input)
     double* d_d = nullptr;
-    double* d_x[2] = {nullptr, nullptr};
+    double* d_x[3] = {nullptr, nullptr, nullptr};
+    int nbuf = 2;                  // iterate buffers in rotation (3 for the persistent variant)
+    bool ns = false;               // neighbour-synchronised FP64 sweeps
+    int* d_dep_ptr = nullptr;      // ctas+1 / neighbour CTAs of each CTA
+    int* d_dep = nullptr;
+    unsigned* d_done = nullptr;    // ctas: sweeps finished in the current launch
+    int64_t dep_edges = 0;
     float* d_e[2] = {nullptr, nullptr};
     float* d_dlt = nullptr;
     Partial* d_part = nullptr;
@@ -197,10 +203,13 @@ DevVec devvec(const jac_ctx* c)
     DevVec v;
     v.x[0] = c->d_x[0];
     v.x[1] = c->d_x[1];
+    v.x[2] = c->d_x[2];
+    v.nbuf = c->nbuf;
     v.e[0] = c->d_e[0];
     v.e[1] = c->d_e[1];
     v.dlt = c->d_dlt;
     v.part = c->d_part;
+    v.dec = c->d_part ? c->d_part + 2 * (size_t)c->nslots : nullptr;
     v.nslots = c->nslots;
     v.trace = c->d_trace;
     return v;
@@ -221,6 +230,9 @@ DevTiles devtiles(const jac_ctx* c)
     t.maxruns = c->maxruns;
     t.ntcap = c->ntcap;
     t.blkcap = c->blkcap;
+    t.dep_ptr = c->d_dep_ptr;
+    t.dep = c->d_dep;
+    t.done = c->d_done;
     return t;
 }
 
@@ -258,6 +270,7 @@ jac_status enqueue_step(jac_ctx* c, bool mixed)
     }
     if (c->variant >= 2) {
         CK(c, launch_reset_bar(c->d_ctl, s));
+        if (c->ns && !mixed) CK(c, cudaMemsetAsync(c->d_done, 0, sizeof(unsigned) * DONE_STRIDE * c->grid, s));
         CK(c, launch_persistent(mixed ? c->pfnmix : c->pfn64, c->grid, c->threads, c->smem, devmat(c), devvec(c),
                                 devtiles(c), c->d_ctl, c->K, s));
     } else {
@@ -377,7 +390,8 @@ void destroy(jac_ctx* c)
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     dfree(c->d_rowptr); dfree(c->d_col); dfree(c->d_S64); dfree(c->d_S32); dfree(c->d_b); dfree(c->d_d);
-    dfree(c->d_x[0]); dfree(c->d_x[1]); dfree(c->d_e[0]); dfree(c->d_e[1]); dfree(c->d_dlt);
+    dfree(c->d_x[0]); dfree(c->d_x[1]); dfree(c->d_x[2]);
+    dfree(c->d_dep_ptr); dfree(c->d_dep); dfree(c->d_done); dfree(c->d_e[0]); dfree(c->d_e[1]); dfree(c->d_dlt);
     dfree(c->d_part); dfree(c->d_ctl); dfree(c->d_hist); dfree(c->d_perm); dfree(c->d_stage); dfree(c->d_stage2);
     dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0); dfree(c->d_cta0);
     dfree(c->d_blk0); dfree(c->d_blk); dfree(c->d_lcol); dfree(c->d_trace);
@@ -438,6 +452,8 @@ jac_status check_opts(const jac_opts& o, jac_ctx* err_ctx)
     if (o.lanes_per_row != 0 && o.lanes_per_row != 1 && o.lanes_per_row != 2 && o.lanes_per_row != 4 &&
         o.lanes_per_row != 8)
         return fail(err_ctx, JAC_EINVAL, "opts.lanes_per_row must be 0, 1, 2, 4 or 8");
+    if (o.sync != JAC_SYNC_GRID && o.sync != JAC_SYNC_NEIGHBOUR)
+        return fail(err_ctx, JAC_EINVAL, "opts.sync must be JAC_SYNC_GRID or JAC_SYNC_NEIGHBOUR");
     return JAC_OK;
 }
 
@@ -467,6 +483,7 @@ double time_per_sweep(jac_ctx* c)
 
 struct Geometry {
     int variant, rows, ctas, lanes;   // lanes 0: automatic
+    int sync = JAC_SYNC_GRID;
 };
 
 }  // namespace
@@ -647,8 +664,9 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
             c->pfn64 = halo_kernel(c->stages, false);
             c->pfnmix = halo_kernel(c->stages, true);
         } else {
-            c->pfn64 = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes);
-            c->pfnmix = persistent_kernel(c->rows_per_tile, c->stages, true, c->lanes);
+            c->ns = c->variant == 2 && c->rows_per_tile == 256 && o.sync == JAC_SYNC_NEIGHBOUR;
+            c->pfn64 = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, c->ns);
+            c->pfnmix = persistent_kernel(c->rows_per_tile, c->stages, true, c->lanes, false);
             c->smem = persistent_smem_bytes(rows, c->emax, c->stages);
         }
         c->threads = (c->variant == 3) ? 256 + 32 : persistent_threads(c->rows_per_tile);
@@ -723,6 +741,29 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
         for (int64_t r = 0; r < n; ++r)
             c->h_row_cost[r] = row_cost ? (*row_cost)[r] : default_row_cost(tf.rowptr[r + 1] - tf.rowptr[r]);
     }
+    std::vector<int32_t> dep_ptr, dep;
+    if (c->ns) {
+        // each CTA's neighbours: the CTAs that own a row it reads (Sec. 4.2.2's
+        // dependency lists at CTA granularity)
+        const int G = c->grid;
+        std::vector<int32_t> cta_of(n);
+        for (int g = 0; g < G; ++g)
+            for (int64_t r = c->h_cta_row0[g]; r < c->h_cta_row0[g + 1]; ++r) cta_of[r] = g;
+        std::vector<int32_t> stamp(G, -1);
+        dep_ptr.assign(G + 1, 0);
+        for (int g = 0; g < G; ++g) {
+            for (int64_t r = c->h_cta_row0[g]; r < c->h_cta_row0[g + 1]; ++r)
+                for (int64_t e = tf.rowptr[r]; e < tf.rowptr[r + 1]; ++e) {
+                    const int h = cta_of[tf.col[e]];
+                    if (h != g && stamp[h] != g) {
+                        stamp[h] = g;
+                        dep.push_back(h);
+                    }
+                }
+            dep_ptr[g + 1] = (int32_t)dep.size();
+        }
+        c->dep_edges = (int64_t)dep.size();
+    }
     c->nslots = c->grid;
 
     // ---- device buffers
@@ -733,13 +774,18 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     CK(nullptr, dalloc(&c->d_d, n + 16));
     CK(nullptr, dalloc(&c->d_x[0], n + 16));
     CK(nullptr, dalloc(&c->d_x[1], n + 16));
+    if (c->variant == 2) {
+        // the persistent kernel rotates its iterate through three buffers (see k_persistent)
+        c->nbuf = 3;
+        CK(nullptr, dalloc(&c->d_x[2], n + 16));
+    }
     if (o.precision == JAC_MIXED) {
         CK(nullptr, dalloc(&c->d_S32, nnz_off + 16));
         CK(nullptr, dalloc(&c->d_e[0], n + 16));
         CK(nullptr, dalloc(&c->d_e[1], n + 16));
         CK(nullptr, dalloc(&c->d_dlt, n + 16));
     }
-    CK(nullptr, dalloc(&c->d_part, 2 * (size_t)c->nslots + 2));
+    CK(nullptr, dalloc(&c->d_part, 2 * (size_t)c->nslots + 4 + 2));
     if (c->variant >= 2) CK(nullptr, dalloc(&c->d_trace, 4 * (size_t)c->grid));
     CK(nullptr, dalloc(&c->d_ctl, 1));
     CK(nullptr, dalloc(&c->d_perm, n));
@@ -760,6 +806,13 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
         CK(nullptr, cudaMemcpy(c->d_blk, win.blk.data(), win.blk.size() * 4, cudaMemcpyHostToDevice));
         if (!win.lcol.empty())
             CK(nullptr, cudaMemcpy(c->d_lcol, win.lcol.data(), win.lcol.size() * 4, cudaMemcpyHostToDevice));
+    }
+    if (c->ns) {
+        CK(nullptr, dalloc(&c->d_dep_ptr, dep_ptr.size()));
+        CK(nullptr, dalloc(&c->d_dep, dep.size() + 1));
+        CK(nullptr, dalloc(&c->d_done, (size_t)DONE_STRIDE * c->grid));
+        CK(nullptr, cudaMemcpy(c->d_dep_ptr, dep_ptr.data(), dep_ptr.size() * 4, cudaMemcpyHostToDevice));
+        if (!dep.empty()) CK(nullptr, cudaMemcpy(c->d_dep, dep.data(), dep.size() * 4, cudaMemcpyHostToDevice));
     }
     if (c->variant >= 2) {
         CK(nullptr, dalloc(&c->d_row0, tl.row0.size()));
@@ -824,6 +877,10 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     if (o.variant || o.tile_rows || o.ctas_per_sm)
         return fail(nullptr, JAC_EINVAL, "autotune needs variant = tile_rows = ctas_per_sm = 0");
     std::vector<Geometry> cand = {{2, 256, 2, 0}, {2, 256, 3, 0}, {2, 224, 0, 0}, {2, 480, 0, 0}, {3, 256, 0, 0}};
+    if (o.precision == JAC_FP64) {
+        cand.push_back({2, 256, 2, 0, JAC_SYNC_NEIGHBOUR});
+        cand.push_back({2, 256, 3, 0, JAC_SYNC_NEIGHBOUR});
+    }
     if (o.lanes_per_row == 0) {
         // the lane counts next to the automatic one (its own arithmetic: see jac_opts.lanes_per_row)
         jac_ctx* probe = nullptr;
@@ -852,6 +909,7 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
         o2.tile_rows = g.rows;
         o2.ctas_per_sm = g.ctas;
         if (g.lanes) o2.lanes_per_row = g.lanes;
+        o2.sync = g.sync;
         jac_ctx* c = nullptr;
         const jac_status st = setup_single(A, b, s, nparts, o2, nullptr, &c);
         if (st != JAC_OK) {
@@ -1079,7 +1137,7 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
         CK(nullptr, dalloc(&c->d_e[1], nv + 16 * nrhs));
         CK(nullptr, dalloc(&c->d_dlt, nv + 16 * nrhs));
     }
-    CK(nullptr, dalloc(&c->d_part, 2 * (size_t)c->nslots + 2));
+    CK(nullptr, dalloc(&c->d_part, 2 * (size_t)c->nslots + 4 + 2));
     CK(nullptr, dalloc(&c->d_ctl, 1));
     CK(nullptr, dalloc(&c->d_bstage, nv + 16));
     CK(nullptr, cudaMallocHost((void**)&c->h_ctl, 2 * sizeof(JacCtl)));
@@ -1355,7 +1413,7 @@ jac_status jac_get_x(jac_ctx* c, double* x, int32_t memory)
     if (!c || !x) return c ? fail(c, JAC_EINVAL, "x is NULL") : JAC_EINVAL;
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
-    const int xb = c->h_ctl[0].xbuf & 1;
+    const int xb = c->h_ctl[0].xbuf;
     double* src = c->d_stage;
     size_t cnt = (size_t)c->n;
     if (c->batched) {
@@ -1474,6 +1532,7 @@ jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
     out->nrhs = c->nrhs;
     out->tile_rows = c->variant >= 2 ? c->rows_per_tile : 0;
     out->lanes_per_row = c->variant >= 2 ? c->lanes : 1;
+    out->sync = c->ns ? JAC_SYNC_NEIGHBOUR : JAC_SYNC_GRID;
     out->ctas_per_sm = (c->variant >= 2 && c->n > 0 && c->grid > 0) ? c->grid / std::max(1, c->sms) : 0;
     return JAC_OK;
 }

@@ -21,6 +21,9 @@ enum : int { PH_P64 = 0, PH_P64R = 1, PH_P32 = 2, PH_P32L = 3 };
 // first CTA writes it back; the host arms it before each call.
 struct JacCtl {
     unsigned long long bar;   // grid-barrier arrivals of the current launch
+    // neighbour-synchronised sweeps (reset with `bar` before every launch):
+    unsigned long long dec_ready;  // sweeps of the launch whose grid-wide residual sums are published
+    unsigned int arrive[4];        // CTAs that finished sweep j, slot j mod 4
     unsigned int ticket;      // last-block detection of the per-sweep launch kernel
     int status;               // ST_* bits
     int done;                 // DONE_*
@@ -65,10 +68,12 @@ struct DevMat {
 };
 
 struct DevVec {
-    double* x[2];             // FP64 iterate y = D x, ping-pong
+    double* x[3];             // FP64 iterate y = D x: nbuf buffers used in rotation
+    int nbuf;                 // 2 (ping-pong) or 3 (neighbour-synchronised sweeps)
     float* e[2];              // FP32 inner iterate f = D e, ping-pong (mixed)
     float* dlt;               // FP32 residual r of the last P64R pass (mixed)
     Partial* part;            // [2][nslots] per-sweep partial norms
+    Partial* dec;             // [4] grid-wide sums of sweep j in slot j mod 4 (neighbour sync)
     int nslots;
     unsigned long long* trace;  // [ctas][4]: compute ns, barrier-wait ns, sweeps, 0 (persistent kernels)
 };
@@ -86,7 +91,14 @@ struct DevTiles {
     int maxruns;              // runs per tile
     int ntcap;                // halo kernel: tile-table capacity per CTA
     int blkcap;               // halo kernel: run-block capacity per CTA (int4)
+    const int* dep_ptr;       // ctas+1: each CTA's neighbours (owners of the rows it reads) ...
+    const int* dep;           // ... as CTA indices (neighbour-synchronised sweeps)
+    unsigned* done;           // ctas x DONE_STRIDE: sweeps each CTA has finished in the current launch
 };
+
+// One 128-byte line per CTA progress flag: every flag has its own writer and
+// several pollers, which would otherwise contend for a few shared lines.
+constexpr int DONE_STRIDE = 32;
 
 // Per-system state of a batched context (systems packed block-diagonally).
 struct DevBatch {
@@ -261,6 +273,18 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ int ld_volatile_i32(const int* p)

@@ -323,7 +323,17 @@ __device__ __forceinline__ void consumer_sync()
 // are dealt round-robin to the 4 sub-partitions, so (math warps + producer)
 // in multiples of 4 per SM leave 128 registers a thread; 2 x 9 warps leave 96.
 // LPR = lanes per row: a tile holds 256/LPR rows, each summed by LPR lanes.
-template <int RPT, int STAGES, bool MIXED, int NWM, int LPR>
+//
+// NS = neighbour-synchronised FP64 sweeps.  Instead of a grid barrier after
+// every sweep, a CTA starts sweep j once (a) the CTAs that own the rows it
+// reads (its dependency list, Sec. 4.2.2) have finished sweep j-1, and (b)
+// the grid-wide residual sums of sweep j-2 are published.  The last CTA to
+// finish a sweep reduces the partial sums once and publishes them; every
+// CTA then takes the same convergence decision for sweep j-2 at its gate of
+// sweep j.  The iterate rotates through three buffers, so when the test of
+// x^k passes, x^k is still intact although sweeps k and k+1 may have run.
+// (b) also orders the overwrite of x^{k-2} after every read of it.
+template <int RPT, int STAGES, bool MIXED, int NWM, int LPR, bool NS>
 __global__ void __maxnreg__(NWM == 8 ? (STAGES == 3 ? 72 : 96) : 128)
 k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
 {
@@ -334,13 +344,16 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     // the FP32 inner sweeps); 8 math warps (96 registers) use the plain loop.
     constexpr bool PIPE = (NWM != 8);
     static_assert(!PIPE || LPR == 1, "the pipelined loop sums a row in one lane");
+    static_assert(!NS || (!MIXED && !PIPE), "neighbour sync is built for the plain FP64 loop");
+    static_assert(!NS || (!MIXED && !PIPE), "neighbour sync is built for the plain FP64 loop");
+    static_assert(!NS || (!MIXED && !PIPE), "neighbour sync is built for the plain FP64 loop");
     const StageLayout L = stage_layout(ROWS, t.emax);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes);
     uint64_t* empty = full + STAGES;
     __shared__ double s_wss[NW];
     __shared__ unsigned long long s_wmx[NW];
     __shared__ long long s_k, s_klim, s_evals, s_outer, s_timeout, s_keval;
-    __shared__ int s_xb, s_phase, s_inner, s_test, s_done, s_start, s_skip, s_fail, s_dec_done;
+    __shared__ int s_xb, s_phase, s_inner, s_test, s_done, s_start, s_skip, s_fail, s_dec_done, s_last, s_stopj;
     __shared__ volatile int s_stop;
     __shared__ double s_relres, s_res2, s_resinf;
 
@@ -461,13 +474,85 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     long long jc = 0;
     int nbar = 0;
     unsigned long long tr_comp = 0, tr_wait = 0, tr_mark = (tid == 0) ? global_ns() : 0;
+    const long long k0 = k;
+    const int xb0 = xb;
+    auto next_buf = [&](int b) { return b + 1 == v.nbuf ? 0 : b + 1; };
+    // Neighbour sync: convergence decision of sweep j from the published sums
+    // (warp 0, lane 0; it has acquired dec_ready > j).  Returns DONE_*.
+    auto ns_decide = [&](int j) -> int {
+        const Partial* ds = v.dec + (j & 3);
+        const double tss = __ldcg(&ds->ss);
+        const unsigned long long tmx = __ldcg(&ds->mx);
+        const Decision d = decide(s_test, ctl->tol, s_klim, ctl->norm_kind, ctl->bnorm, tss, tmx, k0 + j);
+        s_relres = d.relres;
+        s_res2 = d.res2;
+        s_resinf = d.resinf;
+        s_keval = k0 + j;
+        if (d.numeric_bad && blockIdx.x == 0) atomicOr(&ctl->status, ST_NUMERIC);
+        if (blockIdx.x == 0 && ctl->hist && evals < ctl->hist_cap) ctl->hist[evals] = d.relres;
+        evals += 1;
+        return d.done;
+    };
+    // Bounded spin until *p >= target (acquire); false on timeout.
+    auto spin_u64 = [&](const unsigned long long* p, unsigned long long target) -> bool {
+        const long long t0 = clock64();
+        while (ld_acquire_u64(p) < target) {
+            if (ld_volatile_i32(&ctl->status) & ST_TIMEOUT) return false;
+            if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); return false; }
+            __nanosleep(32);
+        }
+        return true;
+    };
+    if (tid == 0) s_stopj = -1;
+    consumer_sync<CT>();
     for (int sw = 0; sw < ksw; ++sw) {
+        if constexpr (NS) {
+            // ---- gate of sweep sw
+            if (sw > 0) {
+                if (warp == 0) {
+                    bool ok = true;
+                    const int d0 = __ldg(t.dep_ptr + blockIdx.x), nd = __ldg(t.dep_ptr + blockIdx.x + 1) - d0;
+                    if (nd <= 32) {
+                        if (lane < nd) {
+                            const unsigned* f = t.done + DONE_STRIDE * __ldg(t.dep + d0 + lane);
+                            const long long t0 = clock64();
+                            while (ld_acquire_u32(f) < (unsigned)sw) {
+                                if (ld_volatile_i32(&ctl->status) & ST_TIMEOUT) { ok = false; break; }
+                                if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); ok = false; break; }
+                                __nanosleep(64);
+                            }
+                        }
+                    } else if (lane == 0) {
+                        // many neighbours: wait for the whole grid instead
+                        ok = spin_u64(&ctl->dec_ready, (unsigned long long)sw);
+                    }
+                    if (sw >= 2 && lane == 0 && ok) ok = spin_u64(&ctl->dec_ready, (unsigned long long)(sw - 1));
+                    __threadfence();
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (lane == 0) {
+                        // every stop state is written before the barrier below,
+                        // so all math threads leave the loop together
+                        if (!ok) {
+                            s_fail = 1;
+                        } else if (sw >= 2) {
+                            const int dn = ns_decide(sw - 2);
+                            if (dn != DONE_RUNNING) { s_done = dn; s_stopj = sw - 2; }
+                        }
+                        const unsigned long long tc_ = global_ns();
+                        tr_wait += tc_ - tr_mark;
+                        tr_mark = tc_;
+                    }
+                }
+                consumer_sync<CT>();
+                if (s_fail || s_stopj >= 0) break;
+            }
+        }
         const int ph = phase_of(MIXED, pos, inner);
         const bool norm_ph = (ph == PH_P64 || ph == PH_P64R);
         double ss = 0.0;
         unsigned long long mx = 0;
         const double* xs = v.x[xb];
-        double* xd = v.x[xb ^ 1];
+        double* xd = v.x[next_buf(xb)];
         const float* es = v.e[pos & 1];
         float* ed = v.e[(pos + 1) & 1];
         // Software pipeline over the sweep's tiles: the x gathers (first chunk of
@@ -637,6 +722,46 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
             const unsigned long long wm = warp_max(mx);
             if (lane == 0) { s_wss[warp] = ws; s_wmx[warp] = wm; }
         }
+        if constexpr (NS) {
+            // ---- publish: partial sums, this CTA's progress flag, and (last
+            // CTA of the sweep) the grid-wide sums of sweep sw
+            consumer_sync<CT>();
+            if (tid == 0) {
+                const unsigned long long tb_ = global_ns();
+                tr_comp += tb_ - tr_mark;
+                tr_mark = tb_;
+                double b = 0.0;
+                unsigned long long bm = 0;
+                for (int w = 0; w < NW; ++w) { b += s_wss[w]; bm = umax64(bm, s_wmx[w]); }
+                Partial* slot = v.part + (sw & 1) * v.nslots + blockIdx.x;
+                __stcg(&slot->ss, b);
+                __stcg(&slot->mx, bm);
+                __threadfence();
+                s_last = 0;
+                if (!(s_skip == (int)blockIdx.x)) {
+                    st_release_u32(t.done + DONE_STRIDE * blockIdx.x, (unsigned)(sw + 1));
+                    s_last = atomicAdd(&ctl->arrive[sw & 3], 1u) == gridDim.x - 1;
+                }
+            }
+            consumer_sync<CT>();
+            if (s_last && warp == 0) {
+                __threadfence();
+                double tss;
+                unsigned long long tmx;
+                reduce_partials_warp(v.part + (sw & 1) * v.nslots, gridDim.x, tss, tmx);
+                if (lane == 0) {
+                    Partial* ds = v.dec + (sw & 3);
+                    __stcg(&ds->ss, tss);
+                    __stcg(&ds->mx, tmx);
+                    ctl->arrive[sw & 3] = 0;            // reused by sweep sw + 4
+                    __threadfence();
+                    atomicMax(&ctl->dec_ready, (unsigned long long)(sw + 1));
+                }
+            }
+            ++nbar;
+            xb = next_buf(xb);
+            continue;
+        }
         consumer_sync<CT>();
         if (tid == 0) {
             const unsigned long long tb_ = global_ns();
@@ -689,7 +814,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
             consumer_sync<CT>();
             evals += 1;
             if (s_dec_done != DONE_RUNNING) { s_done = s_dec_done; break; }
-            if (ph == PH_P64) { k += 1; xb ^= 1; }
+            if (ph == PH_P64) { k += 1; xb = next_buf(xb); }
             else pos = 1;
         } else if (ph == PH_P32) {
             pos += 1;
@@ -699,6 +824,25 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
             outer += 1;
         }
         if (!MIXED && !s_test && k >= s_klim) break;
+    }
+    if constexpr (NS) {
+        // ---- end of the launch: the decisions of the last two sweeps, in order
+        if (!s_fail && s_stopj < 0) {
+            if (tid == 0) {
+                if (nbar > 0 && !spin_u64(&ctl->dec_ready, (unsigned long long)nbar)) s_fail = 1;
+                else
+                    for (int j = nbar >= 2 ? nbar - 2 : 0; j < nbar; ++j) {
+                        const int dn = ns_decide(j);
+                        if (dn != DONE_RUNNING) { s_done = dn; s_stopj = j; break; }
+                    }
+            }
+            consumer_sync<CT>();
+        }
+        // the launch ends at x^{k0+j} (stopped at j) or after its nbar sweeps
+        const int jend = s_stopj >= 0 ? s_stopj : nbar;
+        k = k0 + jend;
+        xb = xb0;
+        for (int j = 0; j < jend; ++j) xb = next_buf(xb);
     }
     // tell the producer to stop issuing; it drains its copies before exiting
     if (tid == 0 && v.trace) {
@@ -1287,20 +1431,20 @@ cudaError_t launch_row_sweep(int ph, const DevMat& m, const DevVec& v, JacCtl* c
     return cudaGetLastError();
 }
 
-template <int RPT, int STAGES, bool MIXED, int NWM, int LPR = 1>
+template <int RPT, int STAGES, bool MIXED, int NWM, int LPR = 1, bool NS = false>
 static const void* persistent_fn()
 {
-    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED, NWM, LPR>);
+    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED, NWM, LPR, NS>);
 }
 
-template <int STAGES, bool MIXED>
+template <int STAGES, bool MIXED, bool NS>
 static const void* persistent_fn_lanes(int lanes)
 {
     switch (lanes) {
-    case 1: return persistent_fn<1, STAGES, MIXED, 8, 1>();
-    case 2: return persistent_fn<1, STAGES, MIXED, 8, 2>();
-    case 4: return persistent_fn<1, STAGES, MIXED, 8, 4>();
-    case 8: return persistent_fn<1, STAGES, MIXED, 8, 8>();
+    case 1: return persistent_fn<1, STAGES, MIXED, 8, 1, NS>();
+    case 2: return persistent_fn<1, STAGES, MIXED, 8, 2, NS>();
+    case 4: return persistent_fn<1, STAGES, MIXED, 8, 4, NS>();
+    case 8: return persistent_fn<1, STAGES, MIXED, 8, 8, NS>();
     default: return nullptr;
     }
 }
@@ -1308,13 +1452,19 @@ static const void* persistent_fn_lanes(int lanes)
 // threads = 32 x math warps: 224 -> 7 (2 CTAs/SM, 128 regs),
 // 256 -> 8 (2 CTAs/SM, 96 regs; or 3 stages, 72 regs, 3 CTAs/SM),
 // 480 -> 15 (1 CTA/SM, 128 regs).  lanes = lanes per row (256 threads only);
-// a tile then holds threads / lanes rows.
-const void* persistent_kernel(int threads, int stages, bool mixed, int lanes)
+// a tile then holds threads / lanes rows.  ns = neighbour-synchronised FP64
+// sweeps (256 threads, FP64 only).
+const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, bool ns)
 {
+    if (ns) {
+        if (mixed || threads != 256) return nullptr;
+        return stages == 3 ? persistent_fn_lanes<3, false, true>(lanes) : persistent_fn_lanes<4, false, true>(lanes);
+    }
     if (threads == 256 && stages == 3)
-        return mixed ? persistent_fn_lanes<3, true>(lanes) : persistent_fn_lanes<3, false>(lanes);
+        return mixed ? persistent_fn_lanes<3, true, false>(lanes) : persistent_fn_lanes<3, false, false>(lanes);
     if (stages != 4) return nullptr;
-    if (threads == 256) return mixed ? persistent_fn_lanes<4, true>(lanes) : persistent_fn_lanes<4, false>(lanes);
+    if (threads == 256)
+        return mixed ? persistent_fn_lanes<4, true, false>(lanes) : persistent_fn_lanes<4, false, false>(lanes);
     if (lanes != 1) return nullptr;
     if (threads == 224) return mixed ? persistent_fn<1, 4, true, 7>() : persistent_fn<1, 4, false, 7>();
     if (threads == 480) return mixed ? persistent_fn<1, 4, true, 15>() : persistent_fn<1, 4, false, 15>();
@@ -1379,7 +1529,8 @@ cudaError_t launch_reset_iterate(JacCtl* ctl, cudaStream_t s)
 
 cudaError_t launch_reset_bar(JacCtl* ctl, cudaStream_t s)
 {
-    return cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned long long), s);
+    // bar, dec_ready and arrive[] are contiguous
+    return cudaMemsetAsync(&ctl->bar, 0, offsetof(JacCtl, ticket) - offsetof(JacCtl, bar), s);
 }
 
 cudaError_t launch_adjoint_grad(const int* rowptr, const int* col, const double* lam, const double* x,

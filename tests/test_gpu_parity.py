@@ -368,6 +368,97 @@ def test_grid_barrier_timeout_is_reported_and_recoverable():
         J.jac_free(ctx)
 
 
+# ------------------------------------------------ neighbour-synchronised sweeps ----
+
+NS = dict(variant=2, sync=J.JAC_SYNC_NEIGHBOUR)
+
+
+@pytest.mark.parametrize("name,A,b", list(_cases()))
+@pytest.mark.parametrize("split,P", SPLITS)
+def test_neighbour_sync_sweeps_equal_grid_barrier_sweeps(name, A, b, split, P):
+    """Neighbour flags order the sweeps exactly like the grid barrier: the same
+    iterate bits after any number of sweeps and graph launch sizes, and the
+    same residual of the last pre-update iterate."""
+    rng = np.random.default_rng(4)
+    x0 = rng.uniform(-1, 1, A.n)
+    ref = _setup(A, b, split, P, variant=2, sweeps_per_graph=64)
+    try:
+        J.jac_set_x(ref, x0)
+        rel_ref = J.jac_sweep(ref, 29)
+        x_ref = J.jac_get_x(ref)
+    finally:
+        J.jac_free(ref)
+    for K, cps in [(64, 2), (1, 3), (2, 2), (7, 3)]:
+        ctx = _setup(A, b, split, P, sweeps_per_graph=K, ctas_per_sm=cps, **NS)
+        try:
+            assert J.jac_stats(ctx)["sync"] == J.JAC_SYNC_NEIGHBOUR
+            J.jac_set_x(ctx, x0)
+            rel = J.jac_sweep(ctx, 29)
+            assert np.array_equal(J.jac_get_x(ctx), x_ref), (K, cps)
+            assert rel == rel_ref
+            assert J.jac_stats(ctx)["k"] == 29
+        finally:
+            J.jac_free(ctx)
+
+
+@pytest.mark.parametrize("split,P", SPLITS)
+@pytest.mark.parametrize("K", [1, 3, 64, 256])
+def test_neighbour_sync_solve_stops_where_the_grid_barrier_stops(split, P, K):
+    """The test of x^k is taken a sweep late but x^k is kept: same stopping
+    sweep, same iterate, same residual history as the grid barrier (and the
+    oracle's 637 sweeps to 1e-6 at 16^3)."""
+    A = W.laplace7(16)
+    xs, b = W.solution_and_rhs(A, 0)
+    out = []
+    for kw in (dict(variant=2), NS):
+        ctx = _setup(A, b, split, P, sweeps_per_graph=K, history=1000, **kw)
+        try:
+            k, rel, st = J.jac_solve(ctx, 1e-6, 5000)
+            out.append((k, rel, st, J.jac_get_x(ctx), J.jac_get_history(ctx)))
+        finally:
+            J.jac_free(ctx)
+    (k0, r0, s0, x0, h0), (k1, r1, s1, x1, h1) = out
+    assert s0 == s1 == J.JAC_OK and k0 == k1 == 637
+    assert r0 == r1 and np.array_equal(x0, x1) and np.array_equal(h0, h1)
+
+
+def test_neighbour_sync_maxit_and_resume():
+    A = W.fe27_deleted(11, seed=2)
+    xs, b = W.solution_and_rhs(A, 5)
+    res = []
+    for kw in (dict(variant=2), NS):
+        ctx = _setup(A, b, "bandrow_nnz", 5, sweeps_per_graph=5, **kw)
+        try:
+            k, rel, st = J.jac_solve(ctx, 1e-30, 23)
+            assert st == J.JAC_ENOTCONV and k == 23
+            k2, rel2, st2 = J.jac_solve(ctx, 1e-30, 31)      # continues from x^23
+            res.append((k, rel, k2, rel2, J.jac_get_x(ctx)))
+        finally:
+            J.jac_free(ctx)
+    assert res[0][:4] == res[1][:4] and np.array_equal(res[0][4], res[1][4])
+
+
+def test_neighbour_sync_timeout_is_reported_and_recoverable():
+    A = W.laplace7(12)
+    xs, b = W.solution_and_rhs(A, 0)
+    ctx = _setup(A, b, "bandrow", 4, fault_skip_cta=3, timeout_cycles=20_000_000, **NS)
+    try:
+        with pytest.raises(J.JacobiError) as e:
+            J.jac_sweep(ctx, 10)
+        assert e.value.status == J.JAC_ETIMEOUT
+    finally:
+        J.jac_free(ctx)
+    ctx = _setup(A, b, "bandrow", 4, **NS)
+    try:
+        J.jac_sweep(ctx, 10)
+        y = np.zeros(A.n)
+        for _ in range(10):
+            y = O.sweep(A, b, y)[0]
+        assert np.linalg.norm(J.jac_get_x(ctx) - y) <= 1e-13 * np.linalg.norm(y)
+    finally:
+        J.jac_free(ctx)
+
+
 def test_autotune_reports_its_choice_and_starts_from_zero():
     A = W.laplace7(24)
     xs, b = W.solution_and_rhs(A, 1)
