@@ -49,6 +49,21 @@ def _algorithmic_bytes(n: int, nnz: int) -> float:
     return 12.0 * off + 8.0 * n + 4.0 * (n + 1) + 8.0 * n + 8.0 * n + 8.0 * n
 
 
+def whole_job_rate(units: float, seconds: float, dist=None, device="cpu"):
+    """Whole-job throughput over ranks: the units all ranks processed divided by
+    the slowest rank's time.  Returns (rate, max_seconds, total_units); without
+    a process group it is the local rate."""
+    if dist is None or not dist.is_available() or not dist.is_initialized():
+        return units / seconds, seconds, units
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item()), float(u.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -420,13 +435,12 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
     sweeps = args.steps * SWEEPS_PER_SPLIT * len(SPLITS)
-    value = ws * bps * sweeps / (total_ms * 1e-3) / 1e9
+    rate, max_s, _ = whole_job_rate(bps * sweeps, total_ms * 1e-3, dist, "cuda")
+    total_ms = max_s * 1e3
+    value = rate / 1e9
+    if dist:
+        dist.barrier()
     launches_per_split = 1 + (SWEEPS_PER_SPLIT + K_PER_GRAPH - 1) // K_PER_GRAPH
     gpu_launches = args.steps * len(SPLITS) * launches_per_split
 
@@ -461,7 +475,7 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = ws * bps * e2e_steps * SWEEPS_PER_SPLIT * len(SPLITS) / e2e_s / 1e9
+    e2e_value = whole_job_rate(bps * e2e_steps * SWEEPS_PER_SPLIT * len(SPLITS), e2e_s, dist, "cuda")[0] / 1e9
     h2d = len(ctxs) * 2 * A.n * 8
     d2h = len(ctxs) * (A.n * 8 + 8)
 
