@@ -41,7 +41,7 @@ struct jac_ctx {
     double* d_b = nullptr;         // b in the new row order (FP64 sweep input)
     double* d_d = nullptr;
     double* d_x[3] = {nullptr, nullptr, nullptr};
-    int nbuf = 2;                  // iterate buffers in rotation (3 for the persistent variant)
+    int nbuf = 2;                  // iterate buffers in rotation (3 with neighbour sync)
     bool ns = false;               // neighbour-synchronised FP64 sweeps
     int* d_dep_ptr = nullptr;      // ctas+1 / neighbour CTAs of each CTA
     int* d_dep = nullptr;
@@ -774,8 +774,10 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     CK(nullptr, dalloc(&c->d_d, n + 16));
     CK(nullptr, dalloc(&c->d_x[0], n + 16));
     CK(nullptr, dalloc(&c->d_x[1], n + 16));
-    if (c->variant == 2) {
-        // the persistent kernel rotates its iterate through three buffers (see k_persistent)
+    if (c->ns) {
+        // neighbour-synchronised sweeps rotate the iterate through three
+        // buffers (see k_persistent); the grid barrier ping-pongs two, which
+        // keeps more of them resident in L2
         c->nbuf = 3;
         CK(nullptr, dalloc(&c->d_x[2], n + 16));
     }
