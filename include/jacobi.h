@@ -70,11 +70,20 @@ typedef enum {
 /* How the persistent kernel orders consecutive sweeps (jac_opts.sync). */
 typedef enum {
     JAC_SYNC_GRID = 0,       /* a grid-wide barrier after every sweep, then the test of that sweep */
-    JAC_SYNC_NEIGHBOUR = 1   /* FP64 sweeps (variant 2, 256 threads): a CTA waits only for the CTAs
+    JAC_SYNC_NEIGHBOUR = 1,  /* FP64 sweeps (variant 2, 256 threads): a CTA waits only for the CTAs
                                 that own the rows it reads (its dependency list, Sec. 4.2.2) and for
                                 the residual sums of the sweep before last; the test of x^k is taken
                                 one sweep later and x^k is kept for it, so results and counts are
                                 those of JAC_SYNC_GRID */
+    JAC_SYNC_ASYNC = 2       /* FP64 (variant 2, 256 threads): asynchronous relaxation, the variant
+                                the paper's conclusion points to (Sec. 5.2): every CTA re-sweeps
+                                its rows with no barrier, in place, so rows read whichever value of
+                                each neighbour is in memory.  Not deterministic.  jac_solve stops
+                                when an estimate from the latest per-CTA residual sums passes the
+                                test, then takes the exact synchronous test of that iterate (and
+                                goes on with synchronous sweeps if it fails): the returned test
+                                value is exact; k counts relaxation passes plus synchronous sweeps.
+                                jac_sweep runs k passes and returns the estimate. */
 } jac_sync;
 
 /* Square sparse matrix in CSR form (Sec. 4.1: AA = val, JA = col, IA = rowptr).
@@ -119,7 +128,8 @@ typedef struct {
                                   a fixed pairwise tree, so iterates are bit-identical across
                                   splittings and tilings for a given L and agree to rounding
                                   across L. */
-    int32_t sync;              /* jac_sync (default JAC_SYNC_GRID; the autotuner tries both) */
+    int32_t sync;              /* jac_sync (default JAC_SYNC_GRID; the autotuner tries grid and
+                                  neighbour; JAC_SYNC_ASYNC only when asked for) */
     int32_t autotune;          /* 1: jac_setup / jac_setup_batched time a few sweeps of every kernel
                                   geometry (variant, tile_rows, ctas_per_sm) and keep the fastest;
                                   jac_setup then re-cuts the CTA row ranges from the measured per-CTA

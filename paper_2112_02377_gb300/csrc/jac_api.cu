@@ -43,6 +43,9 @@ struct jac_ctx {
     double* d_x[3] = {nullptr, nullptr, nullptr};
     int nbuf = 2;                  // iterate buffers in rotation (3 with neighbour sync)
     bool ns = false;               // neighbour-synchronised FP64 sweeps
+    int sync = JAC_SYNC_GRID;      // jac_sync of the FP64 kernel
+    bool certify = false;          // asynchronous contexts: run the grid-synchronised kernel
+    const void* pfn64grid = nullptr;
     int* d_dep_ptr = nullptr;      // ctas+1 / neighbour CTAs of each CTA
     int* d_dep = nullptr;
     unsigned* d_done = nullptr;    // ctas: sweeps finished in the current launch
@@ -79,7 +82,7 @@ struct jac_ctx {
     const void* pfn64 = nullptr;
     const void* pfnmix = nullptr;
     int K = 64;
-    cudaGraphExec_t g64 = nullptr, gmix = nullptr;
+    cudaGraphExec_t g64 = nullptr, gmix = nullptr, gcert = nullptr;
     bool no_graph = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // batched contexts
@@ -271,8 +274,9 @@ jac_status enqueue_step(jac_ctx* c, bool mixed)
     if (c->variant >= 2) {
         CK(c, launch_reset_bar(c->d_ctl, s));
         if (c->ns && !mixed) CK(c, cudaMemsetAsync(c->d_done, 0, sizeof(unsigned) * DONE_STRIDE * c->grid, s));
-        CK(c, launch_persistent(mixed ? c->pfnmix : c->pfn64, c->grid, c->threads, c->smem, devmat(c), devvec(c),
-                                devtiles(c), c->d_ctl, c->K, s));
+        const void* fn = mixed ? c->pfnmix : (c->certify ? c->pfn64grid : c->pfn64);
+        CK(c, launch_persistent(fn, c->grid, c->threads, c->smem, devmat(c), devvec(c), devtiles(c), c->d_ctl, c->K,
+                                s));
     } else {
         if (!mixed) {
             for (int i = 0; i < c->K; ++i) CK(c, launch_row_sweep(PH_P64, devmat(c), devvec(c), c->d_ctl, s));
@@ -288,7 +292,7 @@ jac_status enqueue_step(jac_ctx* c, bool mixed)
 
 jac_status get_graph(jac_ctx* c, bool mixed, cudaGraphExec_t* out)
 {
-    cudaGraphExec_t& g = mixed ? c->gmix : c->g64;
+    cudaGraphExec_t& g = mixed ? c->gmix : (c->certify ? c->gcert : c->g64);
     if (!g) {
         cudaStream_t s = stream_of(c);
         cudaStream_t cap = s;
@@ -387,6 +391,7 @@ void destroy(jac_ctx* c)
     else cudaDeviceSynchronize();
     if (c->g64) cudaGraphExecDestroy(c->g64);
     if (c->gmix) cudaGraphExecDestroy(c->gmix);
+    if (c->gcert) cudaGraphExecDestroy(c->gcert);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     dfree(c->d_rowptr); dfree(c->d_col); dfree(c->d_S64); dfree(c->d_S32); dfree(c->d_b); dfree(c->d_d);
@@ -452,8 +457,8 @@ jac_status check_opts(const jac_opts& o, jac_ctx* err_ctx)
     if (o.lanes_per_row != 0 && o.lanes_per_row != 1 && o.lanes_per_row != 2 && o.lanes_per_row != 4 &&
         o.lanes_per_row != 8)
         return fail(err_ctx, JAC_EINVAL, "opts.lanes_per_row must be 0, 1, 2, 4 or 8");
-    if (o.sync != JAC_SYNC_GRID && o.sync != JAC_SYNC_NEIGHBOUR)
-        return fail(err_ctx, JAC_EINVAL, "opts.sync must be JAC_SYNC_GRID or JAC_SYNC_NEIGHBOUR");
+    if (o.sync != JAC_SYNC_GRID && o.sync != JAC_SYNC_NEIGHBOUR && o.sync != JAC_SYNC_ASYNC)
+        return fail(err_ctx, JAC_EINVAL, "opts.sync must be JAC_SYNC_GRID, JAC_SYNC_NEIGHBOUR or JAC_SYNC_ASYNC");
     return JAC_OK;
 }
 
@@ -664,8 +669,10 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
             c->pfn64 = halo_kernel(c->stages, false);
             c->pfnmix = halo_kernel(c->stages, true);
         } else {
-            c->ns = c->variant == 2 && c->rows_per_tile == 256 && o.sync == JAC_SYNC_NEIGHBOUR;
-            c->pfn64 = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, c->ns);
+            c->sync = (c->variant == 2 && c->rows_per_tile == 256) ? o.sync : JAC_SYNC_GRID;
+            c->ns = c->sync == JAC_SYNC_NEIGHBOUR;
+            c->pfn64 = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, c->sync);
+            c->pfn64grid = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, JAC_SYNC_GRID);
             c->pfnmix = persistent_kernel(c->rows_per_tile, c->stages, true, c->lanes, false);
             c->smem = persistent_smem_bytes(rows, c->emax, c->stages);
         }
@@ -679,13 +686,21 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
                 cudaGetLastError();
                 return 0;
             }
-            int a = 0, b2 = 0;
+            int a = 0, b2 = 0, a3 = 1 << 20;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, c->pfn64, c->threads, smem_bytes) != cudaSuccess ||
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, c->pfnmix, c->threads, smem_bytes) != cudaSuccess) {
                 cudaGetLastError();
                 return 0;
             }
-            return std::min(std::min(a, b2), target_per_sm);
+            if (c->pfn64grid && c->pfn64grid != c->pfn64 &&
+                (cudaFuncSetAttribute(c->pfn64grid, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
+                     cudaSuccess ||
+                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a3, c->pfn64grid, c->threads, smem_bytes) !=
+                     cudaSuccess)) {
+                cudaGetLastError();
+                return 0;
+            }
+            return std::min(std::min(std::min(a, b2), a3), target_per_sm);
         };
         int per_sm = 0;
         if (c->variant == 3) {
@@ -878,8 +893,15 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     // the measured per-CTA compute times while that keeps paying.
     if (o.variant || o.tile_rows || o.ctas_per_sm)
         return fail(nullptr, JAC_EINVAL, "autotune needs variant = tile_rows = ctas_per_sm = 0");
-    std::vector<Geometry> cand = {{2, 256, 2, 0}, {2, 256, 3, 0}, {2, 224, 0, 0}, {2, 480, 0, 0}, {3, 256, 0, 0}};
-    if (o.precision == JAC_FP64) {
+    const bool async = (o.sync == JAC_SYNC_ASYNC);
+    std::vector<Geometry> cand = {{2, 256, 2, 0}, {2, 256, 3, 0}};
+    // asynchronous relaxation runs in the 256-thread geometry only
+    if (!async) {
+        cand.push_back({2, 224, 0, 0});
+        cand.push_back({2, 480, 0, 0});
+        cand.push_back({3, 256, 0, 0});
+    }
+    if (o.precision == JAC_FP64 && !async) {
         cand.push_back({2, 256, 2, 0, JAC_SYNC_NEIGHBOUR});
         cand.push_back({2, 256, 3, 0, JAC_SYNC_NEIGHBOUR});
     }
@@ -911,7 +933,7 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
         o2.tile_rows = g.rows;
         o2.ctas_per_sm = g.ctas;
         if (g.lanes) o2.lanes_per_row = g.lanes;
-        o2.sync = g.sync;
+        o2.sync = async ? JAC_SYNC_ASYNC : g.sync;
         jac_ctx* c = nullptr;
         const jac_status st = setup_single(A, b, s, nparts, o2, nullptr, &c);
         if (st != JAC_OK) {
@@ -1310,7 +1332,27 @@ jac_status jac_sweep(jac_ctx* c, int32_t k, double* relres_out)
     return JAC_OK;
 }
 
+static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out, double* relres_out);
+
 jac_status jac_solve(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out, double* relres_out)
+{
+    if (!c) return JAC_EINVAL;
+    if (c->sync != JAC_SYNC_ASYNC || c->precision != JAC_FP64 || c->batched)
+        return solve_impl(c, tol, maxit, sweeps_out, relres_out);
+    // Asynchronous relaxation until CTA 0's estimate of the test value passes
+    // (or maxit passes), then the synchronous test of the resulting iterate,
+    // which continues with synchronous sweeps if the estimate was optimistic.
+    jac_status st = solve_impl(c, tol, maxit, nullptr, nullptr);
+    if (st != JAC_OK && st != JAC_ENOTCONV) return st;
+    const double ms_async = c->last_ms;
+    c->certify = true;
+    st = solve_impl(c, tol, maxit, sweeps_out, relres_out);
+    c->certify = false;
+    c->last_ms += ms_async;
+    return st;
+}
+
+static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out, double* relres_out)
 {
     if (!c) return JAC_EINVAL;
     if (maxit < 0) return fail(c, JAC_EINVAL, "maxit must be >= 0");
@@ -1534,7 +1576,7 @@ jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
     out->nrhs = c->nrhs;
     out->tile_rows = c->variant >= 2 ? c->rows_per_tile : 0;
     out->lanes_per_row = c->variant >= 2 ? c->lanes : 1;
-    out->sync = c->ns ? JAC_SYNC_NEIGHBOUR : JAC_SYNC_GRID;
+    out->sync = c->sync;
     out->ctas_per_sm = (c->variant >= 2 && c->n > 0 && c->grid > 0) ? c->grid / std::max(1, c->sms) : 0;
     return JAC_OK;
 }

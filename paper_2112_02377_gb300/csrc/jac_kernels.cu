@@ -324,7 +324,10 @@ __device__ __forceinline__ void consumer_sync()
 // in multiples of 4 per SM leave 128 registers a thread; 2 x 9 warps leave 96.
 // LPR = lanes per row: a tile holds 256/LPR rows, each summed by LPR lanes.
 //
-// NS = neighbour-synchronised FP64 sweeps.  Instead of a grid barrier after
+// SYNC orders consecutive sweeps: 0 = grid barrier, 1 = neighbour flags, 2 =
+// none (asynchronous relaxation, see below).
+//
+// SYNC = 1, neighbour-synchronised FP64 sweeps.  Instead of a grid barrier after
 // every sweep, a CTA starts sweep j once (a) the CTAs that own the rows it
 // reads (its dependency list, Sec. 4.2.2) have finished sweep j-1, and (b)
 // the grid-wide residual sums of sweep j-2 are published.  The last CTA to
@@ -333,10 +336,20 @@ __device__ __forceinline__ void consumer_sync()
 // sweep j.  The iterate rotates through three buffers, so when the test of
 // x^k passes, x^k is still intact although sweeps k and k+1 may have run.
 // (b) also orders the overwrite of x^{k-2} after every read of it.
-template <int RPT, int STAGES, bool MIXED, int NWM, int LPR, bool NS>
+//
+// SYNC = 2, asynchronous relaxation (the asynchronous variant the paper points
+// to for many processes, Sec. 5.2 conclusion): each CTA re-sweeps its rows
+// with no barrier, reading and writing one iterate buffer in place, so a row
+// uses whichever value of each neighbour is in memory.  After every pass a
+// CTA publishes its latest residual sums; CTA 0 adds them into an estimate
+// of the test value and stops the launch when it passes.  The estimate mixes
+// passes, so jac_solve certifies the result with a synchronous evaluation.
+template <int RPT, int STAGES, bool MIXED, int NWM, int LPR, int SYNC>
 __global__ void __maxnreg__(NWM == 8 ? (STAGES == 3 ? 72 : 96) : 128)
 k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
 {
+    constexpr bool NS = (SYNC == 1);      // neighbour-synchronised sweeps
+    constexpr bool ASYNC = (SYNC == 2);   // asynchronous (chaotic) relaxation
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int CT = NWM * 32, NW = NWM, ROWS = CT * RPT / LPR;
     // 7 or 15 math warps have 128 registers: software-pipeline the x gathers of
@@ -345,8 +358,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     constexpr bool PIPE = (NWM != 8);
     static_assert(!PIPE || LPR == 1, "the pipelined loop sums a row in one lane");
     static_assert(!NS || (!MIXED && !PIPE), "neighbour sync is built for the plain FP64 loop");
-    static_assert(!NS || (!MIXED && !PIPE), "neighbour sync is built for the plain FP64 loop");
-    static_assert(!NS || (!MIXED && !PIPE), "neighbour sync is built for the plain FP64 loop");
+    static_assert(!ASYNC || (!MIXED && !PIPE), "asynchronous relaxation is built for the plain FP64 loop");
     const StageLayout L = stage_layout(ROWS, t.emax);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes);
     uint64_t* empty = full + STAGES;
@@ -506,6 +518,14 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     if (tid == 0) s_stopj = -1;
     consumer_sync<CT>();
     for (int sw = 0; sw < ksw; ++sw) {
+        if constexpr (ASYNC) {
+            // another CTA (CTA 0) may have stopped the relaxation
+            if (sw > 0) {
+                if (tid == 0 && ld_volatile_i32(&ctl->done) != DONE_RUNNING) s_stopj = sw;
+                consumer_sync<CT>();
+                if (s_stopj >= 0) break;
+            }
+        }
         if constexpr (NS) {
             // ---- gate of sweep sw
             if (sw > 0) {
@@ -552,7 +572,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         double ss = 0.0;
         unsigned long long mx = 0;
         const double* xs = v.x[xb];
-        double* xd = v.x[next_buf(xb)];
+        double* xd = ASYNC ? v.x[xb] : v.x[next_buf(xb)];   // asynchronous: in place
         const float* es = v.e[pos & 1];
         float* ed = v.e[(pos + 1) & 1];
         // Software pipeline over the sweep's tiles: the x gathers (first chunk of
@@ -722,6 +742,47 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
             const unsigned long long wm = warp_max(mx);
             if (lane == 0) { s_wss[warp] = ws; s_wmx[warp] = wm; }
         }
+        if constexpr (ASYNC) {
+            // ---- publish this CTA's latest residual sums; CTA 0 tests their total
+            consumer_sync<CT>();
+            if (tid == 0) {
+                const unsigned long long tb_ = global_ns();
+                tr_comp += tb_ - tr_mark;
+                tr_mark = tb_;
+                double b = 0.0;
+                unsigned long long bm = 0;
+                for (int w = 0; w < NW; ++w) { b += s_wss[w]; bm = umax64(bm, s_wmx[w]); }
+                Partial* slot = v.part + blockIdx.x;
+                __stcg(&slot->ss, b);
+                __stcg(&slot->mx, bm);
+                __threadfence();
+            }
+            if (blockIdx.x == 0) {
+                consumer_sync<CT>();
+                if (warp == 0) {
+                    __threadfence();
+                    double tss;
+                    unsigned long long tmx;
+                    reduce_partials_warp(v.part, gridDim.x, tss, tmx);
+                    if (lane == 0) {
+                        // the passes done so far count as sweeps
+                        const Decision d = decide(s_test, ctl->tol, s_klim, ctl->norm_kind, ctl->bnorm, tss, tmx,
+                                                  k0 + sw + 1);
+                        s_relres = d.relres;
+                        s_res2 = d.res2;
+                        s_resinf = d.resinf;
+                        s_keval = k0 + sw + 1;
+                        if (d.done != DONE_RUNNING) {
+                            s_done = d.done;
+                            if (d.numeric_bad) atomicOr(&ctl->status, ST_NUMERIC);
+                            atomicExch(&ctl->done, d.done);
+                        }
+                    }
+                }
+            }
+            ++nbar;
+            continue;
+        }
         if constexpr (NS) {
             // ---- publish: partial sums, this CTA's progress flag, and (last
             // CTA of the sweep) the grid-wide sums of sweep sw
@@ -824,6 +885,11 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
             outer += 1;
         }
         if (!MIXED && !s_test && k >= s_klim) break;
+    }
+    if constexpr (ASYNC) {
+        k = k0 + nbar;       // passes of this CTA; the iterate stays in its buffer
+        xb = xb0;
+        evals += nbar;
     }
     if constexpr (NS) {
         // ---- end of the launch: the decisions of the last two sweeps, in order
@@ -1431,20 +1497,20 @@ cudaError_t launch_row_sweep(int ph, const DevMat& m, const DevVec& v, JacCtl* c
     return cudaGetLastError();
 }
 
-template <int RPT, int STAGES, bool MIXED, int NWM, int LPR = 1, bool NS = false>
+template <int RPT, int STAGES, bool MIXED, int NWM, int LPR = 1, int SYNC = 0>
 static const void* persistent_fn()
 {
-    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED, NWM, LPR, NS>);
+    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED, NWM, LPR, SYNC>);
 }
 
-template <int STAGES, bool MIXED, bool NS>
+template <int STAGES, bool MIXED, int SYNC>
 static const void* persistent_fn_lanes(int lanes)
 {
     switch (lanes) {
-    case 1: return persistent_fn<1, STAGES, MIXED, 8, 1, NS>();
-    case 2: return persistent_fn<1, STAGES, MIXED, 8, 2, NS>();
-    case 4: return persistent_fn<1, STAGES, MIXED, 8, 4, NS>();
-    case 8: return persistent_fn<1, STAGES, MIXED, 8, 8, NS>();
+    case 1: return persistent_fn<1, STAGES, MIXED, 8, 1, SYNC>();
+    case 2: return persistent_fn<1, STAGES, MIXED, 8, 2, SYNC>();
+    case 4: return persistent_fn<1, STAGES, MIXED, 8, 4, SYNC>();
+    case 8: return persistent_fn<1, STAGES, MIXED, 8, 8, SYNC>();
     default: return nullptr;
     }
 }
@@ -1452,19 +1518,22 @@ static const void* persistent_fn_lanes(int lanes)
 // threads = 32 x math warps: 224 -> 7 (2 CTAs/SM, 128 regs),
 // 256 -> 8 (2 CTAs/SM, 96 regs; or 3 stages, 72 regs, 3 CTAs/SM),
 // 480 -> 15 (1 CTA/SM, 128 regs).  lanes = lanes per row (256 threads only);
-// a tile then holds threads / lanes rows.  ns = neighbour-synchronised FP64
-// sweeps (256 threads, FP64 only).
-const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, bool ns)
+// a tile then holds threads / lanes rows.  sync = 0 grid barrier, 1 neighbour
+// flags, 2 asynchronous relaxation (1 and 2: 256 threads, FP64 only).
+const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, int sync)
 {
-    if (ns) {
+    if (sync == 1 || sync == 2) {
         if (mixed || threads != 256) return nullptr;
-        return stages == 3 ? persistent_fn_lanes<3, false, true>(lanes) : persistent_fn_lanes<4, false, true>(lanes);
+        if (sync == 1)
+            return stages == 3 ? persistent_fn_lanes<3, false, 1>(lanes) : persistent_fn_lanes<4, false, 1>(lanes);
+        return stages == 3 ? persistent_fn_lanes<3, false, 2>(lanes) : persistent_fn_lanes<4, false, 2>(lanes);
     }
+    if (sync != 0) return nullptr;
     if (threads == 256 && stages == 3)
-        return mixed ? persistent_fn_lanes<3, true, false>(lanes) : persistent_fn_lanes<3, false, false>(lanes);
+        return mixed ? persistent_fn_lanes<3, true, 0>(lanes) : persistent_fn_lanes<3, false, 0>(lanes);
     if (stages != 4) return nullptr;
     if (threads == 256)
-        return mixed ? persistent_fn_lanes<4, true, false>(lanes) : persistent_fn_lanes<4, false, false>(lanes);
+        return mixed ? persistent_fn_lanes<4, true, 0>(lanes) : persistent_fn_lanes<4, false, 0>(lanes);
     if (lanes != 1) return nullptr;
     if (threads == 224) return mixed ? persistent_fn<1, 4, true, 7>() : persistent_fn<1, 4, false, 7>();
     if (threads == 480) return mixed ? persistent_fn<1, 4, true, 15>() : persistent_fn<1, 4, false, 15>();

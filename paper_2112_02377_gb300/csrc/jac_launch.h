@@ -11,7 +11,7 @@ cudaError_t launch_row_sweep(int phase, const DevMat& m, const DevVec& v, JacCtl
 
 // Persistent kernel instance for (rows per tile, pipeline stages, mixed cycle);
 // nullptr if that combination is not compiled.
-const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, bool ns);
+const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, int sync);
 int persistent_smem_bytes(int rows, int emax, int stages);
 int persistent_threads(int rows);
 const void* halo_kernel(int stages, bool mixed);

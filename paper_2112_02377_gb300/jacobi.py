@@ -23,7 +23,7 @@ JAC_BANDROW, JAC_BANDROW_NNZ, JAC_SUBSTRUCT = 0, 1, 2
 JAC_MEM_HOST, JAC_MEM_DEVICE = 0, 1
 JAC_FP64, JAC_MIXED = 0, 1
 JAC_NORM_REL2, JAC_NORM_INF = 2, 0
-JAC_SYNC_GRID, JAC_SYNC_NEIGHBOUR = 0, 1
+JAC_SYNC_GRID, JAC_SYNC_NEIGHBOUR, JAC_SYNC_ASYNC = 0, 1, 2
 
 SPLITTINGS = {"bandrow": JAC_BANDROW, "bandrow_nnz": JAC_BANDROW_NNZ, "substruct": JAC_SUBSTRUCT}
 _STATUS_NAMES = ["JAC_OK", "JAC_EINVAL", "JAC_ENOMEM", "JAC_ECUDA", "JAC_ESINGULAR", "JAC_ENOTCONV",

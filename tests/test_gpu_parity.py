@@ -459,6 +459,49 @@ def test_neighbour_sync_timeout_is_reported_and_recoverable():
         J.jac_free(ctx)
 
 
+# ------------------------------------------------ asynchronous relaxation ----
+# Not deterministic: checked by converged-solution parity, never by iterates.
+
+@pytest.mark.parametrize("name,A,b", list(_cases()))
+@pytest.mark.parametrize("split,P", SPLITS)
+def test_async_relaxation_converges_to_the_oracle_solution(name, A, b, split, P):
+    tol = 1e-10
+    xo, ko, relo, sto = O.solve(A, b, tol=tol, maxit=200000)
+    ctx = _setup(A, b, split, P, variant=2, sync=J.JAC_SYNC_ASYNC, sweeps_per_graph=16)
+    try:
+        assert J.jac_stats(ctx)["sync"] == J.JAC_SYNC_ASYNC
+        k, rel, st = J.jac_solve(ctx, tol, 200000)
+        assert st == J.JAC_OK and 0 < k <= 4 * ko
+        x = J.jac_get_x(ctx)
+        true_rel = np.linalg.norm(b - O.spmv(A, x)) / np.linalg.norm(b)
+        assert true_rel <= tol * (1 + 1e-6)                  # the certified test value is exact
+        assert abs(rel - true_rel) <= 1e-13 * (1 + np.linalg.norm(np.abs(A.scipy()) @ np.abs(x)) / np.linalg.norm(b))
+        # both are tol-accurate solutions of A x = b
+        assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+    finally:
+        J.jac_free(ctx)
+
+
+def test_async_relaxation_maxit_and_fixed_passes():
+    A = W.laplace7(14)
+    xs, b = W.solution_and_rhs(A, 2)
+    ctx = _setup(A, b, "bandrow", 4, variant=2, sync=J.JAC_SYNC_ASYNC, sweeps_per_graph=8)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-30, 40)
+        assert st == J.JAC_ENOTCONV and k == 40
+        x = J.jac_get_x(ctx)
+        true_rel = np.linalg.norm(b - O.spmv(A, x)) / np.linalg.norm(b)
+        assert abs(rel - true_rel) <= 1e-12 and true_rel < 1.0
+        J.jac_set_x(ctx, None)
+        J.jac_sweep(ctx, 25)
+        assert J.jac_stats(ctx)["k"] == 25
+        x = J.jac_get_x(ctx)
+        assert np.all(np.isfinite(x))
+        assert np.linalg.norm(b - O.spmv(A, x)) < np.linalg.norm(b)
+    finally:
+        J.jac_free(ctx)
+
+
 def test_autotune_reports_its_choice_and_starts_from_zero():
     A = W.laplace7(24)
     xs, b = W.solution_and_rhs(A, 1)
