@@ -356,6 +356,9 @@ def main():
     ap.add_argument("--profile-rows", type=int, default=0, help="tile rows of the profiling case (0 = default)")
     ap.add_argument("--profile-cps", type=int, default=0, help="CTAs per SM of the profiling case (0 = default)")
     ap.add_argument("--extra", action="store_true", help="run the secondary workloads instead (JSON lines)")
+    ap.add_argument("--clocks-csv", default="",
+                    help="where to keep the nvidia-smi samples of the timed region ({rank} is replaced by the "
+                         "rank); default: a file in the temporary directory")
     ap.add_argument("--pin-geometry", default="",
                     help="ROWS:CTAS_PER_SM: set the contexts up with this kernel geometry and the default CTA "
                          "balance instead of the autotuner (for ncu launch lists, whose serialised timing would "
@@ -428,8 +431,9 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp",
-                                        f"clocks_rank{rank}.csv"))
+    import tempfile
+    clocks = Clocks(local, args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv else
+                    os.path.join(tempfile.gettempdir(), f"jacobi_bench_clocks_rank{rank}.csv"))
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     kernel_ms = 0.0
