@@ -119,3 +119,24 @@ def test_batched_autotune_picks_a_geometry_and_stays_exact():
         xs = x[off * 4:(off + A.n) * 4].reshape(A.n, 4)
         assert np.linalg.norm(xs - y) <= 1e-13 * np.linalg.norm(y)
         off += A.n
+
+
+def test_full_size_256_systems_4_rhs_per_sweep_parity():
+    """The batched benchmark's workload (256 systems, 6.35 M rows, 4 right-hand
+    sides), autotuned: two sweeps of every system and right-hand side against
+    the oracle."""
+    mats, rhs = W.laplace7_batch(256, seed=0, nrhs=4)
+    ctx = J.jac_setup_batched(mats, rhs, J.opts(nrhs=4, autotune=1, sweeps_per_graph=64))
+    try:
+        J.jac_sweep(ctx, 2)
+        x = J.jac_get_x(ctx)
+    finally:
+        J.jac_free(ctx)
+    off = 0
+    for A, b in zip(mats, rhs):
+        y = np.zeros((A.n, 4))
+        for _ in range(2):
+            y = O.sweep_multi(A, b, y)[0]
+        xs = x[off * 4:(off + A.n) * 4].reshape(A.n, 4)
+        assert np.linalg.norm(xs - y) <= 1e-13 * np.linalg.norm(y)
+        off += A.n

@@ -557,17 +557,21 @@ def big():
 
 
 def test_full_size_160cubed_per_sweep_parity_all_splittings(big):
-    """The benchmark's workload and launch configuration: every element of
-    three consecutive sweeps against the oracle fed the same input, for each
-    splitting; then 61 more sweeps and the three iterates compared bit for bit."""
+    """The benchmark's workload and launch configuration (autotuned contexts,
+    64 sweeps per graph): every element of three consecutive sweeps against the
+    oracle fed the same input, for each splitting; then 61 more sweeps and the
+    iterates compared bit for bit (also against the staged-halo kernel and
+    neighbour-synchronised sweeps)."""
     A, b = big
     rng = np.random.default_rng(11)
     x0 = rng.uniform(-1, 1, A.n)
     Mo = O.prepare(A)
-    finals = []
-    for (split, P), variant in [(("bandrow", 64), 3), (("bandrow_nnz", 64), 3), (("substruct", 0), 3),
-                                (("bandrow", 64), 2)]:
-        ctx = _setup(A, b, split, P, variant=variant, sub=(4, 4, 4))
+    finals = {}
+    runs = [(("bandrow", 64), dict(autotune=1)), (("bandrow_nnz", 64), dict(autotune=1)),
+            (("substruct", 0), dict(autotune=1)), (("bandrow", 64), dict(variant=3)),
+            (("substruct", 0), dict(variant=2, sync=J.JAC_SYNC_NEIGHBOUR))]
+    for (split, P), kw in runs:
+        ctx = _setup(A, b, split, P, sub=(4, 4, 4), sweeps_per_graph=64, **kw)
         try:
             J.jac_set_x(ctx, x0)
             x = x0
@@ -579,8 +583,32 @@ def test_full_size_160cubed_per_sweep_parity_all_splittings(big):
                 assert abs(rel - np.sqrt(ss) / np.linalg.norm(b)) <= _relres_tol(A, b, x)
                 x = xg
             J.jac_sweep(ctx, 61)
-            finals.append(J.jac_get_x(ctx))
+            finals.setdefault(J.jac_stats(ctx)["lanes_per_row"], []).append(J.jac_get_x(ctx))
         finally:
             J.jac_free(ctx)
-    for f in finals[1:]:
-        assert np.array_equal(f, finals[0])
+    for group in finals.values():
+        for f in group[1:]:
+            assert np.array_equal(f, group[0])
+
+
+def test_full_size_fe27_128cubed_per_sweep_parity():
+    """FE-like 27-point operator at 128^3 nodes (2.1 M rows, 53.8 M entries),
+    autotuned as in the secondary benchmark: two sweeps element by element."""
+    A = W.fe27_deleted(128, seed=0)
+    xs, b = W.solution_and_rhs(A, 0)
+    rng = np.random.default_rng(12)
+    x0 = rng.uniform(-1, 1, A.n)
+    Mo = O.prepare(A)
+    ctx = _setup(A, b, "bandrow_nnz", 64, autotune=1, sweeps_per_graph=64)
+    try:
+        J.jac_set_x(ctx, x0)
+        x = x0
+        for k in range(2):
+            rel = J.jac_sweep(ctx, 1)
+            xg = J.jac_get_x(ctx)
+            y, ss, mx = O.sweep(Mo, b, x)
+            _assert_sweep_close(A, b, x, xg, y)
+            assert abs(rel - np.sqrt(ss) / np.linalg.norm(b)) <= _relres_tol(A, b, x)
+            x = xg
+    finally:
+        J.jac_free(ctx)
