@@ -70,6 +70,8 @@ struct jac_ctx {
     // tiling / launch
     int* d_row0 = nullptr;
     int* d_nnz0 = nullptr;
+    int* d_row1 = nullptr;         // batched: tile end rows / entries (tiles of active systems only)
+    int* d_nnz1 = nullptr;
     int* d_cta0 = nullptr;
     int* d_blk0 = nullptr;
     int* d_blk = nullptr;
@@ -107,6 +109,10 @@ struct jac_ctx {
     long long* d_sys_off = nullptr;
     double* d_bstage = nullptr;      // n*nrhs staging for batched rhs / x
     std::vector<long long> h_sys_off;
+    std::vector<int32_t> h_rowptr;   // batched: off-diagonal row pointers (tile cuts on re-tiling)
+    int tile_cap = 0, pair_cap = 0;  // batched: capacity of the tile and pair arrays
+    int64_t tiled_rows = 0;          // batched: rows covered by the current tiles
+    bool retiled = false;            // batched: tiles cover a subset of the systems
     // host-side bookkeeping
     int64_t sweeps_total = 0, outer_last = 0;
     double last_ms = 0.0;
@@ -223,6 +229,8 @@ DevTiles devtiles(const jac_ctx* c)
     DevTiles t;
     t.row0 = c->d_row0;
     t.nnz0 = c->d_nnz0;
+    t.row1 = c->d_row1 ? c->d_row1 : (c->d_row0 ? c->d_row0 + 1 : nullptr);
+    t.nnz1 = c->d_nnz1 ? c->d_nnz1 : (c->d_nnz0 ? c->d_nnz0 + 1 : nullptr);
     t.cta0 = c->d_cta0;
     t.blk0 = c->d_blk0;
     t.blk = c->d_blk;
@@ -347,9 +355,16 @@ jac_status run_graph(jac_ctx* c, bool mixed)
 // Batched: gather each right-hand side's current iterate (some stopped ones
 // live in the other ping-pong buffer) into x[0], restart k at 0 and re-arm
 // every system's test.
+jac_status batched_tile(jac_ctx* c, const std::vector<int32_t>& mask, bool alloc = false);
+
 jac_status batched_restart(jac_ctx* c)
 {
     cudaStream_t s = stream_of(c);
+    if (c->retiled) {   // a solve re-tiled for its last systems: every system iterates again
+        CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
+        const jac_status st = batched_tile(c, std::vector<int32_t>());
+        if (st != JAC_OK) return st;
+    }
     CK(c, launch_batched_gather_x(c->d_x[0], c->d_x[1], c->d_row_sys, c->d_mask, c->d_kpar, c->h_ctl[0].xbuf & 1,
                                   c->n, c->nrhs, nullptr, c->d_bstage, s));
     CK(c, cudaMemcpyAsync(c->d_x[0], c->d_bstage, (size_t)c->n * c->nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -398,7 +413,8 @@ void destroy(jac_ctx* c)
     dfree(c->d_x[0]); dfree(c->d_x[1]); dfree(c->d_x[2]);
     dfree(c->d_dep_ptr); dfree(c->d_dep); dfree(c->d_done); dfree(c->d_e[0]); dfree(c->d_e[1]); dfree(c->d_dlt);
     dfree(c->d_part); dfree(c->d_ctl); dfree(c->d_hist); dfree(c->d_perm); dfree(c->d_stage); dfree(c->d_stage2);
-    dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0); dfree(c->d_cta0);
+    dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0);
+    dfree(c->d_row1); dfree(c->d_nnz1); dfree(c->d_cta0);
     dfree(c->d_blk0); dfree(c->d_blk); dfree(c->d_lcol); dfree(c->d_trace);
     dfree(c->d_tile_sys); dfree(c->d_sys_pair0); dfree(c->d_cta_pair0); dfree(c->d_cta_sys0); dfree(c->d_bnorm);
     dfree(c->d_cnt); dfree(c->d_mask); dfree(c->d_ksys); dfree(c->d_kpar); dfree(c->d_rel); dfree(c->d_sys_status);
@@ -490,6 +506,117 @@ struct Geometry {
     int variant, rows, ctas, lanes;   // lanes 0: automatic
     int sync = JAC_SYNC_GRID;
 };
+
+// Batched tiling over the systems still iterating (mask != all right-hand
+// sides stopped; an empty mask = every system): each such system's rows cut
+// into tiles of at most rows_per_tile rows and emax staged entries; CTAs own
+// contiguous tile ranges balanced by the bytes a sweep moves; (CTA, system)
+// partial slots in CTA order, so the slots of one system are contiguous.
+// Fills the tile and pair arrays in place; at set-up (alloc) it first
+// allocates them for the full tiling, which every later subset fits: the
+// cuts of a system do not depend on the other systems, and a CTA has at most
+// one partial slot per tile.
+jac_status batched_tile(jac_ctx* c, const std::vector<int32_t>& mask, bool alloc)
+{
+    const int nsys = c->nsys, R = c->nrhs, G = c->grid;
+    const int all = (1 << R) - 1;
+    const std::vector<long long>& off = c->h_sys_off;
+    const std::vector<int32_t>& rp = c->h_rowptr;
+    std::vector<int32_t> r0v, r1v, p0v, p1v, tsys;
+    int64_t rows_tiled = 0;
+    for (int s = 0; s < nsys; ++s) {
+        if (!mask.empty() && mask[s] == all) continue;
+        long long r = off[s];
+        const long long end = off[s + 1];
+        rows_tiled += end - r;
+        while (r < end) {
+            long long rows = 0, ent = 0;
+            while (r + rows < end && rows < c->rows_per_tile) {
+                const long long len = rp[r + rows + 1] - rp[r + rows];
+                if (rows > 0 && ent + len > c->emax) break;
+                ent += len;
+                ++rows;
+                if (ent > c->emax) break;   // a single oversized row forms its own tile
+            }
+            r0v.push_back((int32_t)r);
+            r1v.push_back((int32_t)(r + rows));
+            p0v.push_back(rp[r]);
+            p1v.push_back(rp[r + rows]);
+            tsys.push_back(s);
+            r += rows;
+        }
+    }
+    const int nt = (int)r0v.size();
+    if (alloc) {
+        c->tile_cap = std::max(nt, 1);
+        c->pair_cap = c->tile_cap + G;
+        CK(c, dalloc(&c->d_row0, (size_t)c->tile_cap + 1));
+        CK(c, dalloc(&c->d_row1, (size_t)c->tile_cap));
+        CK(c, dalloc(&c->d_nnz0, (size_t)c->tile_cap + 1));
+        CK(c, dalloc(&c->d_nnz1, (size_t)c->tile_cap));
+        CK(c, dalloc(&c->d_tile_sys, (size_t)c->tile_cap + 1));
+        CK(c, dalloc(&c->d_cta0, (size_t)G + 1));
+        CK(c, dalloc(&c->d_cta_pair0, (size_t)G));
+        CK(c, dalloc(&c->d_cta_sys0, (size_t)G));
+        CK(c, dalloc(&c->d_sys_pair0, (size_t)nsys + 1));
+        CK(c, dalloc(&c->d_pss, 2 * (size_t)c->pair_cap * R));
+        CK(c, dalloc(&c->d_pmx, 2 * (size_t)c->pair_cap * R));
+    }
+    if (nt > c->tile_cap) return fail(c, JAC_ECUDA, "batched: tile capacity exceeded");
+    std::vector<double> pre(nt + 1, 0.0);
+    for (int i = 0; i < nt; ++i)
+        pre[i + 1] = pre[i] + 12.0 * (p1v[i] - p0v[i]) + (4.0 + 24.0 * R) * (r1v[i] - r0v[i]);
+    std::vector<int32_t> cta0(G + 1, 0);
+    int cur = 0;
+    for (int g = 1; g < G; ++g) {
+        const double target = pre[nt] * (double)g / (double)G;
+        while (cur < nt && pre[cur] + 0.5 * (pre[cur + 1] - pre[cur]) < target) ++cur;
+        cta0[g] = cur;
+    }
+    cta0[G] = nt;
+    std::vector<int32_t> cta_pair0(G, 0), cta_sys0(G, 0), sys_pair0(nsys + 1, -1);
+    int npairs = 0, last_sys = -1;
+    for (int g = 0; g < G; ++g) {
+        cta_pair0[g] = npairs;
+        const int tb = cta0[g], te = cta0[g + 1];
+        if (tb == te) continue;
+        cta_sys0[g] = tsys[tb];
+        for (int i = tb; i < te; ++i) {
+            const int s = tsys[i];
+            if (s == last_sys && i > tb) continue;
+            if (sys_pair0[s] < 0) sys_pair0[s] = npairs;
+            else if (s != last_sys) return fail(c, JAC_ECUDA, "batched: internal tiling error");
+            // every system between the CTA's first and this one gets a slot too (none: systems are tiled in order)
+            last_sys = s;
+            ++npairs;
+        }
+    }
+    // systems without tiles (stopped): an empty slot range at the running position
+    sys_pair0[nsys] = npairs;
+    for (int s = nsys - 1; s >= 0; --s)
+        if (sys_pair0[s] < 0) sys_pair0[s] = sys_pair0[s + 1];
+    if (npairs > c->pair_cap) return fail(c, JAC_ECUDA, "batched: partial-slot capacity exceeded");
+    auto up = [&](int* dst, const std::vector<int32_t>& v) -> cudaError_t {
+        return v.empty() ? cudaSuccess : cudaMemcpy(dst, v.data(), v.size() * 4, cudaMemcpyHostToDevice);
+    };
+    CK(c, up(c->d_row0, r0v));
+    CK(c, up(c->d_row1, r1v));
+    CK(c, up(c->d_nnz0, p0v));
+    CK(c, up(c->d_nnz1, p1v));
+    CK(c, up(c->d_tile_sys, tsys));
+    CK(c, up(c->d_cta0, cta0));
+    CK(c, up(c->d_cta_pair0, cta_pair0));
+    CK(c, up(c->d_cta_sys0, cta_sys0));
+    CK(c, up(c->d_sys_pair0, sys_pair0));
+    c->ntiles = nt;
+    c->npairs = npairs;
+    c->tiled_rows = rows_tiled;
+    c->retiled = !mask.empty();
+    // the captured graphs hold the old tile count: capture again
+    if (c->g64) { cudaGraphExecDestroy(c->g64); c->g64 = nullptr; }
+    if (c->gmix) { cudaGraphExecDestroy(c->gmix); c->gmix = nullptr; }
+    return JAC_OK;
+}
 
 }  // namespace
 
@@ -1121,30 +1248,8 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     if (per_sm < 1) return fail(nullptr, JAC_EINVAL, "batched kernel cannot be made co-resident");
     c->grid = per_sm * prop.multiProcessorCount;
     c->sms = prop.multiProcessorCount;
-    Tiling tl;
-    make_tiling(big, plan, rows, c->emax, c->grid, tl);
-    c->ntiles = (int)tl.ntiles();
-    // (CTA, system) partial slots: pairs ordered by CTA then system; the slots
-    // of one system are contiguous because CTAs own contiguous tile ranges.
-    std::vector<int32_t> cta_pair0(c->grid, 0), cta_sys0(c->grid, 0), sys_pair0(nsys + 1, -1);
-    int npairs = 0, last_sys = -1;
-    for (int g = 0; g < c->grid; ++g) {
-        cta_pair0[g] = npairs;
-        const int tb = tl.cta0[g], te = tl.cta0[g + 1];
-        if (tb == te) continue;
-        const int s0 = tl.tile_part[tb], s1 = tl.tile_part[te - 1];
-        cta_sys0[g] = s0;
-        for (int s = s0; s <= s1; ++s, ++npairs) {
-            if (sys_pair0[s] < 0) sys_pair0[s] = npairs;
-            else if (s != last_sys) return fail(nullptr, JAC_ECUDA, "batched: internal tiling error");
-            last_sys = s;
-        }
-    }
-    sys_pair0[nsys] = npairs;
-    for (int s = 0; s < nsys; ++s)
-        if (sys_pair0[s] < 0) return fail(nullptr, JAC_ECUDA, "batched: a system has no tile");
-    c->npairs = npairs;
     c->nslots = c->grid;
+    c->h_rowptr = big.rowptr;
 
     // ---- device memory
     const size_t nv = (size_t)n * nrhs;
@@ -1168,13 +1273,6 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     std::memset(c->h_ctl, 0, 2 * sizeof(JacCtl));
     CK(nullptr, cudaEventCreate(&c->ev0));
     CK(nullptr, cudaEventCreate(&c->ev1));
-    CK(nullptr, dalloc(&c->d_row0, tl.row0.size()));
-    CK(nullptr, dalloc(&c->d_nnz0, tl.nnz0.size()));
-    CK(nullptr, dalloc(&c->d_cta0, tl.cta0.size()));
-    CK(nullptr, dalloc(&c->d_tile_sys, tl.tile_part.size() + 1));
-    CK(nullptr, dalloc(&c->d_sys_pair0, (size_t)nsys + 1));
-    CK(nullptr, dalloc(&c->d_cta_pair0, (size_t)c->grid));
-    CK(nullptr, dalloc(&c->d_cta_sys0, (size_t)c->grid));
     CK(nullptr, dalloc(&c->d_bnorm, (size_t)nsys * nrhs));
     CK(nullptr, dalloc(&c->d_cnt, 2 * (size_t)nsys));
     CK(nullptr, dalloc(&c->d_mask, (size_t)nsys));
@@ -1183,8 +1281,6 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     CK(nullptr, dalloc(&c->d_rel, (size_t)nsys * nrhs));
     CK(nullptr, dalloc(&c->d_sys_status, (size_t)nsys));
     CK(nullptr, dalloc(&c->d_ndone, 1));
-    CK(nullptr, dalloc(&c->d_pss, 2 * (size_t)std::max(npairs, 1) * nrhs));
-    CK(nullptr, dalloc(&c->d_pmx, 2 * (size_t)std::max(npairs, 1) * nrhs));
     CK(nullptr, dalloc(&c->d_row_sys, (size_t)n));
     CK(nullptr, dalloc(&c->d_sys_off, (size_t)nsys + 1));
     auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
@@ -1202,14 +1298,11 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
         CK(nullptr, up(c->d_S32, t32.data(), nnz_off * 4));
     }
     CK(nullptr, up(c->d_d, big.d.data(), n * 8));
-    CK(nullptr, up(c->d_row0, tl.row0.data(), tl.row0.size() * 4));
-    CK(nullptr, up(c->d_nnz0, tl.nnz0.data(), tl.nnz0.size() * 4));
-    CK(nullptr, up(c->d_cta0, tl.cta0.data(), tl.cta0.size() * 4));
-    CK(nullptr, up(c->d_tile_sys, tl.tile_part.data(), tl.tile_part.size() * 4));
-    CK(nullptr, up(c->d_sys_pair0, sys_pair0.data(), sys_pair0.size() * 4));
-    CK(nullptr, up(c->d_cta_pair0, cta_pair0.data(), cta_pair0.size() * 4));
-    CK(nullptr, up(c->d_cta_sys0, cta_sys0.data(), cta_sys0.size() * 4));
     CK(nullptr, up(c->d_row_sys, row_sys.data(), row_sys.size() * 4));
+    {
+        const jac_status st_t = batched_tile(C, std::vector<int32_t>(), true);
+        if (st_t != JAC_OK) return fail(nullptr, st_t, C->err);
+    }
     CK(nullptr, up(c->d_sys_off, off.data(), off.size() * 8));
     // right-hand sides: packed n x nrhs, then c = b / a_ii and ||b_s,q||
     cudaStream_t sm = stream_of(C);
@@ -1399,6 +1492,22 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
         cudaError_t e = cudaEventSynchronize(ea);
         if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "solve loop"); }
         if (ha->done != DONE_RUNNING || ha->status != 0) break;
+        if (c->batched) {
+            // Systems that have stopped leave their CTAs idle while the grid waits
+            // for the rest: once the rows still iterating fall below 70 % of the
+            // tiled rows, cut tiles over those systems only (between launches).
+            std::vector<int32_t> mask(c->nsys);
+            CK(c, cudaStreamSynchronize(s));
+            CK(c, cudaMemcpy(mask.data(), c->d_mask, mask.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            const int all = (1 << c->nrhs) - 1;
+            int64_t active = 0;
+            for (int q = 0; q < c->nsys; ++q)
+                if (mask[q] != all) active += c->h_sys_off[q + 1] - c->h_sys_off[q];
+            if (active > 0 && active * 10 < c->tiled_rows * 7) {
+                st = batched_tile(c, mask);
+                if (st != JAC_OK) { cleanup(); return st; }
+            }
+        }
         const long long prog = ha->k * 4 + ha->phase + ha->evals;
         if (prog == last_k) {
             if (++stalled > 4) {

@@ -123,7 +123,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
     __shared__ double s_wss[NW][NRHS];
     __shared__ unsigned long long s_wmx[NW][NRHS];
     __shared__ long long s_k, s_klim, s_evals, s_outer, s_timeout;
-    __shared__ int s_xb, s_phase, s_inner, s_test, s_start, s_fail, s_stop_all, s_norm;
+    __shared__ int s_xb, s_phase, s_inner, s_test, s_start, s_fail, s_stop_all, s_norm, s_blast;
     __shared__ double s_tol;
     __shared__ volatile int s_stop;
 
@@ -201,8 +201,8 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
                 const int ph = phase_of(MIXED, MIXED ? (phase0 + sw) % inner : 0, inner);
                 const bool fp64 = (ph == PH_P64 || ph == PH_P64R);
                 unsigned char* st = smem + sidx * L.bytes;
-                const int r0 = __ldg(t.row0 + ti), r1 = __ldg(t.row0 + ti + 1);
-                const int p0 = __ldg(t.nnz0 + ti), p1 = __ldg(t.nnz0 + ti + 1);
+                const int r0 = __ldg(t.row0 + ti), r1 = __ldg(t.row1 + ti);
+                const int p0 = __ldg(t.nnz0 + ti), p1 = __ldg(t.nnz1 + ti);
                 const bool over = (p1 - p0) > emax;
                 unsigned bytes = 0;
                 int vb = 0, ve = 0, cb = 0, ce = 0;
@@ -245,7 +245,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
     long long evals = s_evals, outer = s_outer;
     long long jc = 0;
     int nbar = 0;
-    const int my_pair0 = bt.cta_pair0[blockIdx.x], my_sys0 = bt.cta_sys0[blockIdx.x];
+    const int my_pair0 = bt.cta_pair0[blockIdx.x];
     for (int sw = 0; sw < ksw; ++sw) {
         const int ph = phase_of(MIXED, pos, inner);
         const bool norm_ph = (ph == PH_P64 || ph == PH_P64R);
@@ -256,6 +256,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
         double ss[NRHS];
         unsigned long long mx[NRHS];
         int cur = -1, msk = ALL;
+        int pidx = -1;   // the CTA's partial slot of the current system: systems met so far - 1
         // per-(CTA, system) partials: block reduction, then the last CTA of the system decides
         auto finish = [&](int sys) {
 #pragma unroll
@@ -266,7 +267,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
             }
             b_consumer_sync(CT);
             if (tid == 0) {
-                const int slot = my_pair0 + (sys - my_sys0);
+                const int slot = my_pair0 + pidx;
                 const int par = sw & 1;
                 for (int q = 0; q < NRHS; ++q) {
                     double a = 0.0;
@@ -277,19 +278,35 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
                 }
                 __threadfence();
                 const unsigned arrived = atomicAdd(bt.cnt + par * bt.nsys + sys, 1u);
-                if (arrived == (unsigned)(__ldg(bt.sys_pair0 + sys + 1) - __ldg(bt.sys_pair0 + sys)) - 1) {
-                    __threadfence();
+                s_blast = arrived == (unsigned)(__ldg(bt.sys_pair0 + sys + 1) - __ldg(bt.sys_pair0 + sys)) - 1;
+            }
+            b_consumer_sync(CT);
+            // the last CTA of the system: warp 0 adds the system's (CTA, system)
+            // partials, lane-strided then a fixed shuffle tree
+            if (s_blast && warp == 0) {
+                __threadfence();
+                const int pb = __ldg(bt.sys_pair0 + sys), pe = __ldg(bt.sys_pair0 + sys + 1);
+                const int par = sw & 1;
+                double ta[NRHS];
+                unsigned long long tm[NRHS];
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q) {
+                    double a = 0.0;
+                    unsigned long long b2 = 0;
+                    for (int pp = pb + lane; pp < pe; pp += 32) {
+                        a += __ldcg(bt.pss + ((size_t)par * bt.npairs + pp) * NRHS + q);
+                        b2 = umax64(b2, __ldcg(bt.pmx + ((size_t)par * bt.npairs + pp) * NRHS + q));
+                    }
+                    ta[q] = warp_sum(a);
+                    tm[q] = warp_max(b2);
+                }
+                if (lane == 0) {
                     bt.cnt[par * bt.nsys + sys] = 0;
-                    const int pb = __ldg(bt.sys_pair0 + sys), pe = __ldg(bt.sys_pair0 + sys + 1);
                     int mk = ld_volatile_i32(bt.mask + sys);
                     for (int q = 0; q < NRHS; ++q) {
                         if (mk & (1 << q)) continue;
-                        double a = 0.0;
-                        unsigned long long b2 = 0;
-                        for (int pp = pb; pp < pe; ++pp) {
-                            a += __ldcg(bt.pss + ((size_t)par * bt.npairs + pp) * NRHS + q);
-                            b2 = umax64(b2, __ldcg(bt.pmx + ((size_t)par * bt.npairs + pp) * NRHS + q));
-                        }
+                        const double a = ta[q];
+                        const unsigned long long b2 = tm[q];
                         const double bn = bt.bnorm[sys * NRHS + q];
                         const Decision d = decide(s_test, s_tol, s_klim, s_norm, bn, a, b2, k);
                         bt.rel[sys * NRHS + q] = d.relres;
@@ -320,6 +337,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
             if (sys != cur) {
                 if (cur >= 0 && msk != ALL && norm_ph) finish(cur);
                 cur = sys;
+                ++pidx;
                 msk = ld_volatile_i32(bt.mask + sys);
 #pragma unroll
                 for (int q = 0; q < NRHS; ++q) { ss[q] = 0.0; mx[q] = 0; }
@@ -337,8 +355,8 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
             }
             if (ok && msk != ALL) {
                 const unsigned char* st = smem + sidx * L.bytes;
-                const int r0 = __ldg(t.row0 + ti), r1 = __ldg(t.row0 + ti + 1);
-                const int p0 = __ldg(t.nnz0 + ti), p1 = __ldg(t.nnz0 + ti + 1);
+                const int r0 = __ldg(t.row0 + ti), r1 = __ldg(t.row1 + ti);
+                const int p0 = __ldg(t.nnz0 + ti), p1 = __ldg(t.nnz1 + ti);
                 const bool over = (p1 - p0) > emax;
                 const int* srp = reinterpret_cast<const int*>(st + L.o_rp) - (r0 & ~3);
                 const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (p0 & ~3);

@@ -79,8 +79,10 @@ struct DevVec {
 };
 
 struct DevTiles {
-    const int* row0;          // ntiles+1
-    const int* nnz0;          // ntiles+1
+    const int* row0;          // ntiles+1: first row of each tile (tile i ends where i+1 starts) ...
+    const int* nnz0;          // ntiles+1: first entry of each tile ...
+    const int* row1;          // ntiles: ... or, where the tiles skip rows, end row of each tile
+    const int* nnz1;          // ntiles: ... and end entry (batched kernel; row0 + 1 / nnz0 + 1 otherwise)
     const int* cta0;          // ctas+1
     const int* blk0;          // ntiles+1 (halo kernel): int4 offset of each tile's run block
     const int* blk;           // run blocks {xlen, own, nruns, flags} + {src, len, dst, 0} x nruns
