@@ -144,14 +144,15 @@ def _geometry(st) -> dict:
     v, rows, cps = st["variant"], st["tile_rows"], st["ctas_per_sm"]
     if v == 2:
         sync = st["sync"] if st["precision"] == 0 else 0
-        name = (f"k_persistent<1,{3 if cps == 3 else 4},{'true' if st['precision'] == 1 else 'false'},"
+        name = (f"k_persistent<1,{st['stages']},{'true' if st['precision'] == 1 else 'false'},"
                 f"{rows // 32},{st['lanes_per_row']},{sync}>")
     elif v == 3:
         name = "k_halo<3,false>"
     else:
         name = "k_row_sweep"
     return {"kernel": name, "variant": v, "tile_rows": rows, "ctas_per_sm": cps,
-            "lanes_per_row": st["lanes_per_row"], "sync": st["sync"], "ctas": st["ctas"], "tiles": st["ntiles"]}
+            "lanes_per_row": st["lanes_per_row"], "sync": st["sync"], "stages": st["stages"], "ctas": st["ctas"],
+            "tiles": st["ntiles"]}
 
 
 def _kernel_hash() -> str:

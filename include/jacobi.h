@@ -128,6 +128,8 @@ typedef struct {
                                   a fixed pairwise tree, so iterates are bit-identical across
                                   splittings and tilings for a given L and agree to rounding
                                   across L. */
+    int32_t stages;            /* variant 2, 256 threads, 2 CTAs/SM: pipeline stages 0 = auto (4), or 3 / 2
+                                  larger stages (36 / 54 KB) that hold whole tiles of long rows */
     int32_t sync;              /* jac_sync (default JAC_SYNC_GRID; the autotuner tries grid and
                                   neighbour; JAC_SYNC_ASYNC only when asked for) */
     int32_t autotune;          /* 1: jac_setup / jac_setup_batched time a few sweeps of every kernel
@@ -167,6 +169,7 @@ typedef struct {
     int32_t tile_rows, ctas_per_sm;  /* kernel geometry in use (chosen by the autotuner if enabled) */
     int32_t lanes_per_row;           /* lanes per row in use (a tile holds tile_rows / lanes_per_row rows) */
     int32_t sync;                    /* jac_sync in use for FP64 sweeps */
+    int32_t stages;                  /* pipeline stages of the persistent kernels */
 } jac_stats_t;
 
 /* Defaults for every option. */

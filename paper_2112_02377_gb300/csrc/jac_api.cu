@@ -473,6 +473,8 @@ jac_status check_opts(const jac_opts& o, jac_ctx* err_ctx)
     if (o.lanes_per_row != 0 && o.lanes_per_row != 1 && o.lanes_per_row != 2 && o.lanes_per_row != 4 &&
         o.lanes_per_row != 8)
         return fail(err_ctx, JAC_EINVAL, "opts.lanes_per_row must be 0, 1, 2, 4 or 8");
+    if (o.stages != 0 && o.stages != 2 && o.stages != 3 && o.stages != 4)
+        return fail(err_ctx, JAC_EINVAL, "opts.stages must be 0, 2, 3 or 4");
     if (o.sync != JAC_SYNC_GRID && o.sync != JAC_SYNC_NEIGHBOUR && o.sync != JAC_SYNC_ASYNC)
         return fail(err_ctx, JAC_EINVAL, "opts.sync must be JAC_SYNC_GRID, JAC_SYNC_NEIGHBOUR or JAC_SYNC_ASYNC");
     return JAC_OK;
@@ -505,6 +507,7 @@ double time_per_sweep(jac_ctx* c)
 struct Geometry {
     int variant, rows, ctas, lanes;   // lanes 0: automatic
     int sync = JAC_SYNC_GRID;
+    int stages = 0;                   // 0: automatic
 };
 
 // Batched tiling over the systems still iterating (mask != all right-hand
@@ -762,6 +765,9 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     if (c->variant == 3 && c->rows_per_tile != 256) c->variant = 2;
     const int target_per_sm = (c->variant == 2 && c->rows_per_tile == 256 && o.ctas_per_sm == 3) ? 3 : 2;
     if (target_per_sm == 3) c->stages = 3;
+    // fewer, larger stages (2 CTAs/SM, 256 threads): room for whole tiles of long rows
+    if (c->variant == 2 && c->rows_per_tile == 256 && target_per_sm == 2 && (o.stages == 2 || o.stages == 3))
+        c->stages = o.stages;
     // Lanes per row (256-thread geometry only): long rows fill a stage's
     // entry budget with few rows, which leaves math warps without a row, and
     // a long FMA chain per thread; L lanes per row split both.  Each lane's
@@ -787,8 +793,11 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
             c->maxruns = 16;
             stage_budget = 36 * 1024 - (c->xcap + 8) * 8;
         } else {
-            // 2 CTAs/SM x 4 stages for 224/256-row tiles, 1 CTA/SM x 4 stages for 480-row tiles
-            stage_budget = rows <= 256 ? 26 * 1024 : 52 * 1024;
+            // 2 CTAs/SM x 4 stages for 224/256-thread tiles (or 3 / 2 larger
+            // stages), 3 CTAs/SM x 3 stages, 1 CTA/SM x 4 stages for 480-row tiles
+            stage_budget = c->rows_per_tile <= 256 ? 26 * 1024 : 52 * 1024;
+            if (c->rows_per_tile == 256 && target_per_sm == 2 && c->stages == 3) stage_budget = 36 * 1024;
+            if (c->rows_per_tile == 256 && target_per_sm == 2 && c->stages == 2) stage_budget = 54 * 1024;
         }
         const int64_t budget_entries = std::max<int64_t>(rows, (stage_budget - 16 * rows - 1024) / 12);
         c->emax = (int)std::min<int64_t>(cap_entries, budget_entries);
@@ -1047,6 +1056,13 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
                     cand.push_back({2, 256, 2, L});
                     cand.push_back({2, 256, 3, L});
                 }
+            // long rows: larger stages hold whole tiles of 256/L rows
+            if (la >= 2)
+                for (int L : {la, la * 2})
+                    if (L <= 8) {
+                        cand.push_back({2, 256, 2, L, JAC_SYNC_GRID, 3});
+                        cand.push_back({2, 256, 2, L, JAC_SYNC_GRID, 2});
+                    }
         }
     }
     jac_ctx* best = nullptr;
@@ -1060,6 +1076,7 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
         o2.tile_rows = g.rows;
         o2.ctas_per_sm = g.ctas;
         if (g.lanes) o2.lanes_per_row = g.lanes;
+        o2.stages = g.stages;
         o2.sync = async ? JAC_SYNC_ASYNC : g.sync;
         jac_ctx* c = nullptr;
         const jac_status st = setup_single(A, b, s, nparts, o2, nullptr, &c);
@@ -1686,6 +1703,7 @@ jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
     out->tile_rows = c->variant >= 2 ? c->rows_per_tile : 0;
     out->lanes_per_row = c->variant >= 2 ? c->lanes : 1;
     out->sync = c->sync;
+    out->stages = c->variant >= 2 ? c->stages : 0;
     out->ctas_per_sm = (c->variant >= 2 && c->n > 0 && c->grid > 0) ? c->grid / std::max(1, c->sms) : 0;
     return JAC_OK;
 }

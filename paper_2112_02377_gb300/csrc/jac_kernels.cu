@@ -345,7 +345,7 @@ __device__ __forceinline__ void consumer_sync()
 // of the test value and stops the launch when it passes.  The estimate mixes
 // passes, so jac_solve certifies the result with a synchronous evaluation.
 template <int RPT, int STAGES, bool MIXED, int NWM, int LPR, int SYNC>
-__global__ void __maxnreg__(NWM == 8 ? (STAGES == 3 ? 72 : 96) : 128)
+__global__ void __maxnreg__(NWM == 8 ? (STAGES == 3 ? 72 : 96) : 128)   // STAGES 3 with 8 math warps: 3 CTAs/SM
 k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
 {
     constexpr bool NS = (SYNC == 1);      // neighbour-synchronised sweeps
@@ -1531,6 +1531,8 @@ const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, in
     if (sync != 0) return nullptr;
     if (threads == 256 && stages == 3)
         return mixed ? persistent_fn_lanes<3, true, 0>(lanes) : persistent_fn_lanes<3, false, 0>(lanes);
+    if (threads == 256 && stages == 2)
+        return mixed ? persistent_fn_lanes<2, true, 0>(lanes) : persistent_fn_lanes<2, false, 0>(lanes);
     if (stages != 4) return nullptr;
     if (threads == 256)
         return mixed ? persistent_fn_lanes<4, true, 0>(lanes) : persistent_fn_lanes<4, false, 0>(lanes);

@@ -54,7 +54,8 @@ class jac_opts(ctypes.Structure):
                 ("inner_sweeps", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("subdomains", ctypes.c_int32 * 3),
                 ("node_of_row", ctypes.c_void_p), ("nrhs", ctypes.c_int32), ("transpose", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("lanes_per_row", ctypes.c_int32), ("sync", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("lanes_per_row", ctypes.c_int32), ("stages", ctypes.c_int32), ("sync", ctypes.c_int32),
+                ("autotune", ctypes.c_int32),
                 ("history", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("timeout_cycles", ctypes.c_uint64),
                 ("fault_skip_cta", ctypes.c_int32), ("device", ctypes.c_int32)]
@@ -68,7 +69,7 @@ class jac_stats_t(ctypes.Structure):
                [(f, ctypes.c_double) for f in ("last_relres", "last_res2", "last_resinf", "last_ms",
                                                  "bytes_per_sweep_fp64", "bytes_per_sweep_fp32")] + \
                [(f, ctypes.c_int32) for f in ("variant", "precision", "splitting", "nrhs", "tile_rows",
-                                                "ctas_per_sm", "lanes_per_row", "sync")]
+                                                "ctas_per_sm", "lanes_per_row", "sync", "stages")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
