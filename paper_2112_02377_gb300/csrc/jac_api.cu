@@ -376,6 +376,8 @@ jac_status batched_restart(jac_ctx* c)
 
 jac_status status_from_ctl(jac_ctx* c, const JacCtl& h)
 {
+    if (h.status & ST_CONFIG)
+        return fail(c, JAC_ECUDA, "a kernel was launched with less shared memory than its stage layout needs");
     if (h.status & ST_TIMEOUT)
         return fail(c, JAC_ETIMEOUT, "a device-side wait exceeded its bound (grid barrier or copy); iterate undefined");
     if ((h.status & ST_NUMERIC) || h.done == DONE_NUMERIC)

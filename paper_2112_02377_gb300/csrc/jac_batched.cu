@@ -141,15 +141,20 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
         s_test = c->test;
         s_tol = c->tol;
         s_norm = c->norm_kind;
-        s_start = (c->done == DONE_RUNNING) && (c->status == 0);
+        // the stages and their barriers must fit the dynamic shared memory of the launch
+        const bool fits = (unsigned long long)STAGES * L.bytes + 2ull * STAGES * 8 <= dynamic_smem_bytes();
+        if (!fits) atomicOr(&ctl->status, ST_CONFIG);
+        s_start = fits && (c->done == DONE_RUNNING) && (c->status == 0);
         s_stop = 0;
         s_fail = 0;
         s_stop_all = 0;
-        for (int q = 0; q < STAGES; ++q) {
-            mbar_init(&full[q], 1);
-            mbar_init(&empty[q], NW);
+        if (fits) {
+            for (int q = 0; q < STAGES; ++q) {
+                mbar_init(&full[q], 1);
+                mbar_init(&empty[q], NW);
+            }
+            fence_mbar_init();
         }
-        fence_mbar_init();
     }
     __syncthreads();
     if (!s_start) return;

@@ -8,7 +8,16 @@
 namespace jac {
 
 // Status bits written by kernels into JacCtl::status.
-enum : int { ST_TIMEOUT = 1, ST_NUMERIC = 2 };
+// ST_CONFIG: the launch gave a kernel less dynamic shared memory than its
+// stage layout needs (it then touches nothing and returns).
+enum : int { ST_TIMEOUT = 1, ST_NUMERIC = 2, ST_CONFIG = 4 };
+
+__device__ __forceinline__ unsigned dynamic_smem_bytes()
+{
+    unsigned v;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
 // JacCtl::done values.
 enum : int { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_LIMIT = 2, DONE_NUMERIC = 3 };
 // Sweep phases, in the diagonally scaled variables y = D x, f = D e (see

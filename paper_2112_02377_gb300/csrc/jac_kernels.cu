@@ -383,18 +383,23 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         s_test = c->test;
         s_done = c->done;
         s_skip = c->fault_skip_cta;
-        s_start = (c->done == DONE_RUNNING) && (c->status == 0);
+        // the stages and their barriers must fit the dynamic shared memory of the launch
+        const bool fits = (unsigned long long)STAGES * L.bytes + 2ull * STAGES * 8 <= dynamic_smem_bytes();
+        if (!fits) atomicOr(&ctl->status, ST_CONFIG);
+        s_start = fits && (c->done == DONE_RUNNING) && (c->status == 0);
         s_relres = c->relres;
         s_res2 = c->res2;
         s_resinf = c->resinf;
         s_keval = c->k_eval;
         s_stop = 0;
         s_fail = 0;
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NW);
+        if (fits) {
+            for (int s = 0; s < STAGES; ++s) {
+                mbar_init(&full[s], 1);
+                mbar_init(&empty[s], NW);
+            }
+            fence_mbar_init();
         }
-        fence_mbar_init();
     }
     __syncthreads();
     if (!s_start) return;
@@ -998,6 +1003,9 @@ k_halo(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     uint64_t* fmat = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(s_blk) + t.blkcap * 16);
     uint64_t* fx = fmat + STAGES;
     uint64_t* empty = fx + STAGES;
+    // the stages, the tile table and the barriers must fit the launch's dynamic shared memory
+    const bool halo_fits =
+        (unsigned long long)(reinterpret_cast<unsigned char*>(empty + STAGES) - smem) <= dynamic_smem_bytes();
     __shared__ double s_wss[NW];
     __shared__ unsigned long long s_wmx[NW];
     __shared__ long long s_k, s_klim, s_evals, s_outer, s_timeout, s_keval;
@@ -1020,7 +1028,8 @@ k_halo(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         s_test = c->test;
         s_done = c->done;
         s_skip = c->fault_skip_cta;
-        s_start = (c->done == DONE_RUNNING) && (c->status == 0) && nt <= t.ntcap;
+        if (!halo_fits) atomicOr(&ctl->status, ST_CONFIG);
+        s_start = halo_fits && (c->done == DONE_RUNNING) && (c->status == 0) && nt <= t.ntcap;
         s_relres = c->relres;
         s_res2 = c->res2;
         s_resinf = c->resinf;
@@ -1028,15 +1037,17 @@ k_halo(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         s_stop = 0;
         s_epoch = 0;
         s_fail = 0;
-        for (int q = 0; q < STAGES; ++q) {
-            mbar_init(&fmat[q], 1);
-            mbar_init(&fx[q], 1);
-            mbar_init(&empty[q], NW);
+        if (halo_fits) {
+            for (int q = 0; q < STAGES; ++q) {
+                mbar_init(&fmat[q], 1);
+                mbar_init(&fx[q], 1);
+                mbar_init(&empty[q], NW);
+            }
+            fence_mbar_init();
         }
-        fence_mbar_init();
     }
     // the CTA's tile table (constant for the launch)
-    if (nt <= t.ntcap) {
+    if (halo_fits && nt <= t.ntcap) {
         const int bbase = __ldg(t.blk0 + tb);
         for (int i = tid; i <= nt; i += blockDim.x) {
             s_row0[i] = __ldg(t.row0 + tb + i);
@@ -1524,9 +1535,17 @@ const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, in
 {
     if (sync == 1 || sync == 2) {
         if (mixed || threads != 256) return nullptr;
-        if (sync == 1)
-            return stages == 3 ? persistent_fn_lanes<3, false, 1>(lanes) : persistent_fn_lanes<4, false, 1>(lanes);
-        return stages == 3 ? persistent_fn_lanes<3, false, 2>(lanes) : persistent_fn_lanes<4, false, 2>(lanes);
+        // every stage count gets its own instantiation: the kernel's stage
+        // layout must match the shared memory the launch provides
+        switch (stages * 4 + sync) {
+        case 2 * 4 + 1: return persistent_fn_lanes<2, false, 1>(lanes);
+        case 3 * 4 + 1: return persistent_fn_lanes<3, false, 1>(lanes);
+        case 4 * 4 + 1: return persistent_fn_lanes<4, false, 1>(lanes);
+        case 2 * 4 + 2: return persistent_fn_lanes<2, false, 2>(lanes);
+        case 3 * 4 + 2: return persistent_fn_lanes<3, false, 2>(lanes);
+        case 4 * 4 + 2: return persistent_fn_lanes<4, false, 2>(lanes);
+        default: return nullptr;
+        }
     }
     if (sync != 0) return nullptr;
     if (threads == 256 && stages == 3)

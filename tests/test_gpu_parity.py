@@ -502,6 +502,32 @@ def test_async_relaxation_maxit_and_fixed_passes():
         J.jac_free(ctx)
 
 
+@pytest.mark.parametrize("stages", [2, 3, 4])
+def test_every_stage_count_with_every_sync_mode(stages):
+    """Each (stages, sync) pair runs its own kernel instantiation: neighbour
+    sync gives the grid barrier's bits, asynchronous relaxation converges."""
+    A = W.fe27_deleted(12, seed=4)
+    xs, b = W.solution_and_rhs(A, 3)
+    out = {}
+    for sync in (J.JAC_SYNC_GRID, J.JAC_SYNC_NEIGHBOUR):
+        ctx = _setup(A, b, "bandrow_nnz", 4, variant=2, stages=stages, sync=sync, sweeps_per_graph=9)
+        try:
+            assert J.jac_stats(ctx)["stages"] == stages
+            J.jac_sweep(ctx, 31)
+            out[sync] = J.jac_get_x(ctx)
+        finally:
+            J.jac_free(ctx)
+    assert np.array_equal(out[J.JAC_SYNC_GRID], out[J.JAC_SYNC_NEIGHBOUR])
+    ctx = _setup(A, b, "bandrow_nnz", 4, variant=2, stages=stages, sync=J.JAC_SYNC_ASYNC, sweeps_per_graph=9)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-10, 100000)
+        assert st == J.JAC_OK
+        x = J.jac_get_x(ctx)
+        assert np.linalg.norm(b - O.spmv(A, x)) / np.linalg.norm(b) <= 1e-10 * (1 + 1e-6)
+    finally:
+        J.jac_free(ctx)
+
+
 def test_autotune_reports_its_choice_and_starts_from_zero():
     A = W.laplace7(24)
     xs, b = W.solution_and_rhs(A, 1)
