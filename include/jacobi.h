@@ -132,6 +132,9 @@ typedef struct {
                                   larger stages (36 / 54 KB) that hold whole tiles of long rows */
     int32_t sync;              /* jac_sync (default JAC_SYNC_GRID; the autotuner tries grid and
                                   neighbour; JAC_SYNC_ASYNC only when asked for) */
+    int32_t debug;             /* 1: canary bytes in the 16-element padding after every device vector of
+                                  jac_setup contexts, checked after each jac_sweep / jac_solve; a
+                                  write past the end of a vector returns JAC_ECUDA */
     int32_t autotune;          /* 1: jac_setup / jac_setup_batched time a few sweeps of every kernel
                                   geometry (variant, tile_rows, ctas_per_sm) and keep the fastest;
                                   jac_setup then re-cuts the CTA row ranges from the measured per-CTA

@@ -113,6 +113,13 @@ struct jac_ctx {
     int tile_cap = 0, pair_cap = 0;  // batched: capacity of the tile and pair arrays
     int64_t tiled_rows = 0;          // batched: rows covered by the current tiles
     bool retiled = false;            // batched: tiles cover a subset of the systems
+    // opts.debug: canary bytes in the padding after device vectors
+    struct Canary {
+        const char* name;
+        unsigned char* at;
+        size_t bytes;
+    };
+    std::vector<Canary> canaries;
     // host-side bookkeeping
     int64_t sweeps_total = 0, outer_last = 0;
     double last_ms = 0.0;
@@ -356,6 +363,36 @@ jac_status run_graph(jac_ctx* c, bool mixed)
 // live in the other ping-pong buffer) into x[0], restart k at 0 and re-arm
 // every system's test.
 jac_status batched_tile(jac_ctx* c, const std::vector<int32_t>& mask, bool alloc = false);
+
+// ---------------------------------------------------------------- canaries
+// With opts.debug every device vector's 16-element padding (past the last
+// element any kernel may write) holds a byte pattern that is checked after
+// each sweep or solve call: a stray write past the end shows up as an error.
+constexpr unsigned char CANARY = 0xA5;
+
+template <class T>
+void add_canary(jac_ctx* c, const char* name, T* base, size_t used)
+{
+    if (base) c->canaries.push_back({name, reinterpret_cast<unsigned char*>(base + used), 16 * sizeof(T)});
+}
+
+jac_status set_canaries(jac_ctx* c)
+{
+    for (const auto& k : c->canaries) CK(c, cudaMemset(k.at, CANARY, k.bytes));
+    return JAC_OK;
+}
+
+jac_status check_canaries(jac_ctx* c)
+{
+    std::vector<unsigned char> h;
+    for (const auto& k : c->canaries) {
+        h.assign(k.bytes, 0);
+        CK(c, cudaMemcpy(h.data(), k.at, k.bytes, cudaMemcpyDeviceToHost));
+        for (unsigned char v : h)
+            if (v != CANARY) return fail(c, JAC_ECUDA, std::string("device buffer overrun detected past ") + k.name);
+    }
+    return JAC_OK;
+}
 
 jac_status batched_restart(jac_ctx* c)
 {
@@ -1000,6 +1037,24 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
         CK(nullptr, cudaMemcpy(c->d_orow, P.rowptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
         if (P.nnz()) CK(nullptr, cudaMemcpy(c->d_ocol, P.col.data(), P.nnz() * 4, cudaMemcpyHostToDevice));
     }
+    if (o.debug) {
+        const size_t nn = (size_t)n;
+        add_canary(C, "rowptr", c->d_rowptr, nn + 1);
+        add_canary(C, "col", c->d_col, (size_t)nnz_off);
+        add_canary(C, "S64", c->d_S64, (size_t)nnz_off);
+        add_canary(C, "S32", c->d_S32, (size_t)nnz_off);
+        add_canary(C, "b", c->d_b, nn);
+        add_canary(C, "d", c->d_d, nn);
+        add_canary(C, "x[0]", c->d_x[0], nn);
+        add_canary(C, "x[1]", c->d_x[1], nn);
+        add_canary(C, "x[2]", c->d_x[2], nn);
+        add_canary(C, "e[0]", c->d_e[0], nn);
+        add_canary(C, "e[1]", c->d_e[1], nn);
+        add_canary(C, "r (FP32)", c->d_dlt, nn);
+        add_canary(C, "stage", c->d_stage, nn);
+        const jac_status stc = set_canaries(C);
+        if (stc != JAC_OK) return fail(nullptr, stc, C->err);
+    }
     // right-hand side and control block
     cudaStream_t sm = stream_of(C);
     if (b) {
@@ -1441,6 +1496,7 @@ jac_status jac_sweep(jac_ctx* c, int32_t k, double* relres_out)
     if (st != JAC_OK) return st;
     c->sweeps_total += h.evals;
     if (relres_out) *relres_out = h.relres;
+    if (!c->canaries.empty()) return check_canaries(c);
     return JAC_OK;
 }
 
@@ -1575,6 +1631,10 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
     }
     if (sweeps_out) *sweeps_out = h.k;
     if (relres_out) *relres_out = h.relres;
+    if (!c->canaries.empty()) {
+        const jac_status stc = check_canaries(c);
+        if (stc != JAC_OK) return stc;
+    }
     if (h.done == DONE_LIMIT) return fail(c, JAC_ENOTCONV, "maxit reached before the tolerance");
     if (h.done != DONE_CONVERGED) return fail(c, JAC_ECUDA, "solve ended in an unexpected state");
     return JAC_OK;

@@ -55,7 +55,7 @@ class jac_opts(ctypes.Structure):
                 ("node_of_row", ctypes.c_void_p), ("nrhs", ctypes.c_int32), ("transpose", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("lanes_per_row", ctypes.c_int32), ("stages", ctypes.c_int32), ("sync", ctypes.c_int32),
-                ("autotune", ctypes.c_int32),
+                ("debug", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("history", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("timeout_cycles", ctypes.c_uint64),
                 ("fault_skip_cta", ctypes.c_int32), ("device", ctypes.c_int32)]

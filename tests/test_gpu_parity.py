@@ -528,6 +528,39 @@ def test_every_stage_count_with_every_sync_mode(stages):
         J.jac_free(ctx)
 
 
+@pytest.mark.parametrize("kw", [dict(variant=1), dict(variant=2), dict(variant=3), dict(variant=2, lanes_per_row=4),
+                                dict(variant=2, stages=2, lanes_per_row=2), dict(variant=2, sync=J.JAC_SYNC_NEIGHBOUR),
+                                dict(variant=2, sync=J.JAC_SYNC_ASYNC), dict(variant=2, precision=J.JAC_MIXED),
+                                dict(variant=2, tile_rows=480, precision=J.JAC_MIXED)])
+def test_no_kernel_writes_past_a_device_vector(kw):
+    """Canary bytes after every device vector (opts.debug) survive sweeps and
+    solves of every kernel form, on a ragged problem."""
+    A = W.fe27_deleted(10, seed=6)
+    xs, b = W.solution_and_rhs(A, 4)
+    ctx = _setup(A, b, "bandrow_nnz", 3, debug=1, sweeps_per_graph=5, inner_sweeps=8, **kw)
+    try:
+        J.jac_sweep(ctx, 13)
+        J.jac_solve(ctx, 1e-9, 20000)
+        J.jac_set_x(ctx, xs)
+        J.jac_sweep(ctx, 2)
+        assert np.all(np.isfinite(J.jac_get_x(ctx)))
+    finally:
+        J.jac_free(ctx)
+
+
+def test_nan_in_b_is_reported():
+    A = W.laplace7(8)
+    xs, b = W.solution_and_rhs(A, 0)
+    b[17] = np.nan
+    ctx = _setup(A, b, "bandrow", 2, variant=2)
+    try:
+        with pytest.raises(J.JacobiError) as e:
+            J.jac_solve(ctx, 1e-8, 1000)
+        assert e.value.status == J.JAC_ENUMERIC
+    finally:
+        J.jac_free(ctx)
+
+
 def test_autotune_reports_its_choice_and_starts_from_zero():
     A = W.laplace7(24)
     xs, b = W.solution_and_rhs(A, 1)
