@@ -178,3 +178,26 @@ def test_autotune_rejects_a_fixed_geometry_before_touching_the_gpu():
     with pytest.raises(J.JacobiError) as e:
         J.jac_setup_batched([A], [b], J.opts(autotune=1, tile_rows=96))
     assert "autotune" in str(e.value)
+
+
+def test_empty_system_is_rejected():
+    E = W.CSR(0, np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32), np.zeros(0))
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_partition_plan(E, J.JAC_BANDROW, 1, J.opts())
+    assert ei.value.status == J.JAC_EINVAL and "empty" in str(ei.value)
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("lanes_per_row", 3, "lanes_per_row"),
+    ("stages", 5, "stages"),
+    ("sync", 7, "sync"),
+    ("tile_rows", 100, "tile_rows"),
+    ("ctas_per_sm", 4, "ctas_per_sm"),
+    ("inner_sweeps", 1, "inner_sweeps"),
+    ("norm", 1, "norm"),
+])
+def test_option_values_are_checked_before_any_device_call(field, value, msg):
+    A = W.laplace7(4)
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup(A, np.ones(A.n), J.JAC_BANDROW, 2, J.opts(**{field: value}))
+    assert ei.value.status == J.JAC_EINVAL and msg in str(ei.value)
