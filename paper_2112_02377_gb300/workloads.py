@@ -24,12 +24,16 @@ those files are not available, so these synthetic families stand in for them):
                          f = cos(x + y) (the paper's Set-1 problem, Sec. 5.1.1).
 * ``convection7``     -- small non-symmetric 7-point operator (diffusion plus
                          first-order upwind convection), used to exercise A^T.
+* ``random_irregular`` -- unstructured diagonally dominant matrix with an
+                         irregular row-length mix (a few rows longer than a
+                         staged tile), entries in random column order.
 * ``paper_csr_example`` / ``paper_pattern_10x10`` -- the small matrices printed
                          in the paper (Sec. 4.1 CSR example, Sec. 4.2.2 three-band
                          example).
 
 Every matrix is returned as a :class:`CSR` whose rows keep their entries in
-ascending column order.  Row ``r`` of a grid matrix sits at grid node
+ascending column order (``random_irregular`` excepted: its rows are shuffled,
+to exercise the stored-order summation).  Row ``r`` of a grid matrix sits at grid node
 ``node[r]`` (``i + gx*(j + gy*k)``); ``node is None`` means the natural
 ordering ``node[r] == r``.
 """
@@ -61,7 +65,10 @@ class CSR:
         return int(self.rowptr[-1])
 
     def scipy(self) -> sp.csr_matrix:
-        return sp.csr_matrix((self.val, self.col, self.rowptr), shape=(self.n, self.n))
+        """A scipy copy.  The arrays are copied: scipy canonicalises a matrix
+        in place (sorts each row's columns), which would change the stored
+        entry order of this CSR and with it the order of every row's sum."""
+        return sp.csr_matrix((self.val.copy(), self.col.copy(), self.rowptr.copy()), shape=(self.n, self.n))
 
     def stats(self) -> dict:
         """Matrix statistics in the columns the paper tabulates (Sec. 5.1.3)."""
@@ -406,3 +413,32 @@ def random_dominant(n: int, seed: int, density: float = 0.05, margin: float = 0.
     sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
     np.fill_diagonal(M, d * sign)
     return dense_to_csr(M)
+
+
+def random_irregular(n: int, seed: int, long_rows: int = 2, long_len: int = 3000, margin: float = 0.1) -> CSR:
+    """Sparse strictly diagonally dominant matrix with an irregular row-length
+    mix: most rows 2-8 off-diagonal entries, a quarter 9-40, a few 41-200, and
+    ``long_rows`` rows of ``long_len`` entries (longer than a staged tile).
+    Columns uniform over the other rows, values U[-1, 1], each row's entries
+    stored in random column order."""
+    rng = np.random.default_rng(seed)
+    u = rng.random(n)
+    lens = np.where(u < 0.70, rng.integers(2, 9, n), np.where(u < 0.95, rng.integers(9, 41, n),
+                                                               rng.integers(41, 201, n)))
+    for r in rng.choice(n, size=min(long_rows, n), replace=False):
+        lens[r] = long_len
+    lens = np.minimum(lens, n - 1)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    cols, vals = [], []
+    for i in range(n):
+        c = rng.choice(n - 1, size=int(lens[i]), replace=False)
+        c = c + (c >= i)                          # skip the diagonal
+        v = rng.uniform(-1.0, 1.0, size=c.size)
+        d = (1.0 + margin) * np.abs(v).sum() + 0.1
+        d = d if rng.random() < 0.5 else -d
+        k = rng.integers(0, c.size + 1)           # the diagonal at a random place in the row
+        cols.append(np.insert(c, k, i))
+        vals.append(np.insert(v, k, d))
+        rowptr[i + 1] = rowptr[i] + c.size + 1
+    return CSR(n, rowptr.astype(np.int32), np.concatenate(cols).astype(np.int32), np.concatenate(vals),
+               name=f"irregular_{n}_{seed}")

@@ -561,6 +561,53 @@ def test_nan_in_b_is_reported():
         J.jac_free(ctx)
 
 
+# ------------------------------------------------ irregular matrices, option mix ----
+
+_OPTION_MIX = [dict(variant=1), dict(variant=3), dict(variant=2), dict(variant=2, ctas_per_sm=3),
+               dict(variant=2, tile_rows=224), dict(variant=2, tile_rows=480),
+               dict(variant=2, sync=J.JAC_SYNC_NEIGHBOUR), dict(variant=2, stages=2, sync=J.JAC_SYNC_NEIGHBOUR),
+               dict(variant=2, lanes_per_row=2), dict(variant=2, lanes_per_row=2, stages=3),
+               dict(variant=2, lanes_per_row=4, ctas_per_sm=3), dict(variant=2, lanes_per_row=8, stages=2)]
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_irregular_rows_under_every_option_mix(seed):
+    """Row lengths from 2 to 200 plus rows longer than a staged tile, entries
+    in random order: per-sweep parity with the oracle for every kernel form,
+    and one bit pattern per lane count across kernel forms and splittings."""
+    A = W.random_irregular(20000 if seed == 1 else 7000, seed)
+    rng = np.random.default_rng(seed + 40)
+    b = rng.uniform(-1, 1, A.n)
+    x0 = rng.uniform(-1, 1, A.n)
+    Mo = O.prepare(A)
+    y1 = O.sweep(Mo, b, x0)[0]
+    y2, ss2, _ = O.sweep(Mo, b, y1)
+    finals = {}
+    for i, kw in enumerate(_OPTION_MIX):
+        split, P = [("bandrow", 5), ("bandrow_nnz", 13)][i % 2]
+        ctx = _setup(A, b, split, P, sweeps_per_graph=3, **kw)
+        try:
+            J.jac_set_x(ctx, x0)
+            J.jac_sweep(ctx, 1)
+            x1 = J.jac_get_x(ctx)
+            _assert_sweep_close(A, b, x0, x1, y1)
+            J.jac_set_x(ctx, y1)                    # the oracle's iterate as input: a clean second step
+            rel = J.jac_sweep(ctx, 1)
+            _assert_sweep_close(A, b, y1, J.jac_get_x(ctx), y2)
+            assert abs(rel - np.sqrt(ss2) / np.linalg.norm(b)) <= _relres_tol(A, b, y1)
+            J.jac_set_x(ctx, x0)
+            J.jac_sweep(ctx, 11)
+            finals.setdefault(J.jac_stats(ctx)["lanes_per_row"], []).append((kw, split, J.jac_get_x(ctx)))
+        finally:
+            J.jac_free(ctx)
+    for group in finals.values():
+        kw0, s0, f0 = group[0]
+        for kw, sp, f in group[1:]:
+            bad = np.flatnonzero(f != f0)
+            assert bad.size == 0, (f"{kw} {sp} differs from {kw0} {s0} in {bad.size} rows, first {bad[:5]}, "
+                                   f"row lengths {np.diff(A.rowptr)[bad[:5]]}")
+
+
 def test_autotune_reports_its_choice_and_starts_from_zero():
     A = W.laplace7(24)
     xs, b = W.solution_and_rhs(A, 1)

@@ -201,3 +201,21 @@ def test_option_values_are_checked_before_any_device_call(field, value, msg):
     with pytest.raises(J.JacobiError) as ei:
         J.jac_setup(A, np.ones(A.n), J.JAC_BANDROW, 2, J.opts(**{field: value}))
     assert ei.value.status == J.JAC_EINVAL and msg in str(ei.value)
+
+
+def test_irregular_workload_shape_and_scipy_copy_keeps_stored_order():
+    """The irregular input has unsorted rows, a diagonal at a random place and
+    strict row dominance; handing it to scipy (which sorts in place) must not
+    reorder the caller's entries, since the entry order fixes every row sum."""
+    A = W.random_irregular(3000, 3)
+    lens = np.diff(A.rowptr)
+    assert lens.max() == min(3001, A.n) and (lens >= 3).all()
+    col0, val0 = A.col.copy(), A.val.copy()
+    unsorted = sum(np.any(np.diff(A.col[A.rowptr[i]:A.rowptr[i + 1]]) < 0) for i in range(A.n))
+    assert unsorted > A.n // 2
+    _ = abs(A.scipy()) @ np.ones(A.n)
+    assert np.array_equal(A.col, col0) and np.array_equal(A.val, val0)
+    D = A.scipy()
+    diag = np.abs(D.diagonal())
+    off = np.asarray(abs(D).sum(axis=1)).ravel() - diag
+    assert (diag > off).all()
