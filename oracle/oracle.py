@@ -26,6 +26,10 @@ partitioned procedures"):
 * ``partitioned_sweep``   -- one sweep per partition on a private copy of x
   holding only owned and received entries (the CPU stand-in for the MPI
   exchange).
+* ``split_prepare`` / ``split_sweep`` / ``split_solve`` -- substructuring with
+  the interface block split between subdomains (Sec. 4.3): local matrices
+  A_s with A33 = sum_s A33^(s), the two-step product (local sums, then
+  assembly at the interface) and the weighted interface dot product.
 * ``adjoint_gradients``   -- dL/db = lambda, dL/dA_ij = -lambda_i x_j with
   A^T lambda = dL/dx, the lambda solve done by the same Jacobi loop.
 
@@ -76,7 +80,10 @@ def _c():
             L.jo_partitioned_sweep.argtypes = [i64, P, P, P, P, P, P, P, i64, P, P, P, P, P, P, P]
             L.jo_spmv.argtypes = [i64, P, P, P, P, P]
             L.jo_sweep_multi.argtypes = [i64, i64, P, P, P, P, P, P, P, P, P, P]
-            for f in (L.jo_diag, L.jo_sweep, L.jo_solve, L.jo_partitioned_sweep, L.jo_sweep_multi):
+            L.jo_split_diag.argtypes = [i64, i64, P, P, P, P, P, P]
+            L.jo_split_sweep.argtypes = [i64, P, i64, P, P, P, P, P, P, P, P, P, P, P, P, P]
+            for f in (L.jo_diag, L.jo_sweep, L.jo_solve, L.jo_partitioned_sweep, L.jo_sweep_multi,
+                      L.jo_split_diag, L.jo_split_sweep):
                 f.restype = ctypes.c_int
             L.jo_spmv.restype = None
             _lib = L
@@ -341,6 +348,94 @@ def partitioned_sweep(A, b: np.ndarray, x: np.ndarray, part_ptr: np.ndarray, row
     if st == JO_EHALO:
         raise LookupError("a row read an x entry missing from its dependency list")
     return y, ss.value, mx.value
+
+
+# ---------------------------------------------------------------------------
+# Substructuring with the interface block split between subdomains (Sec. 4.3)
+# ---------------------------------------------------------------------------
+
+class _Split:
+    """Local matrices of all subdomains stacked in subdomain order, with
+    global columns, and the assembled diagonal (computed once)."""
+
+    def __init__(self, locals_, n: int):
+        self.n = int(n)
+        self.nsub = len(locals_)
+        ptr, rows, cols, vals, grow = [0], [np.zeros(1, np.int64)], [], [], []
+        for L in locals_:
+            l2g = np.asarray(L.l2g, dtype=np.int64)
+            rp = np.asarray(L.rowptr, dtype=np.int64)
+            rows.append(rows[-1][-1] + rp[1:])
+            cols.append(l2g[np.asarray(L.col, dtype=np.int64)])
+            vals.append(np.asarray(L.val, dtype=np.float64))
+            grow.append(l2g)
+            ptr.append(ptr[-1] + L.n)
+        self.sub_ptr = np.array(ptr, dtype=np.int64)
+        self.rowptr = np.ascontiguousarray(np.concatenate(rows), dtype=np.int64)
+        self.gcol = np.ascontiguousarray(np.concatenate(cols) if cols else np.zeros(0), dtype=np.int32)
+        self.val = np.ascontiguousarray(np.concatenate(vals) if vals else np.zeros(0), dtype=np.float64)
+        self.grow = np.ascontiguousarray(np.concatenate(grow) if grow else np.zeros(0), dtype=np.int32)
+        self.mult = np.bincount(self.grow, minlength=self.n).astype(np.int32)
+        if (self.mult == 0).any():
+            raise ValueError("a node belongs to no subdomain")
+        self.d = np.empty(self.n)
+        self.dinv = np.empty(self.n)
+        st = _c().jo_split_diag(int(self.sub_ptr[-1]), self.n, _p(self.rowptr), _p(self.gcol), _p(self.val),
+                                _p(self.grow), _p(self.d), _p(self.dinv))
+        if st != JO_OK:
+            raise ZeroDivisionError("zero assembled diagonal entry")
+
+    def interface(self) -> np.ndarray:
+        """Global nodes held by two or more subdomains (the interface set)."""
+        return np.flatnonzero(self.mult >= 2)
+
+
+def split_prepare(locals_, n: int) -> _Split:
+    """Stack the local matrices (each with ``n``, ``rowptr``, ``col``, ``val``,
+    ``l2g``) and assemble the diagonal once."""
+    return _Split(locals_, n)
+
+
+def split_sweep(P: _Split, b: np.ndarray, x: np.ndarray, want_r: bool = False):
+    """One Jacobi sweep in the split form: local off-diagonal sums per
+    subdomain, assembly at the interface in subdomain order, the update with
+    the assembled diagonal, and the weighted interface dot product.
+
+    Returns (x_next, sumsq, maxabs[, r]) of the pre-update iterate x."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(P.n)
+    r = np.empty(P.n) if want_r else None
+    ss = ctypes.c_double()
+    mx = ctypes.c_double()
+    _c().jo_split_sweep(P.nsub, _p(P.sub_ptr), P.n, _p(P.rowptr), _p(P.gcol), _p(P.val), _p(P.grow),
+                        _p(P.mult), _p(P.d), _p(P.dinv), _p(b), _p(x), _p(y), _p(r) if want_r else None,
+                        ctypes.byref(ss), ctypes.byref(mx))
+    if want_r:
+        return y, ss.value, mx.value, r
+    return y, ss.value, mx.value
+
+
+def split_solve(P: _Split, b: np.ndarray, x0: Optional[np.ndarray] = None, tol: float = 1e-8,
+                maxit: int = 100000, norm: int = 2):
+    """Algorithm 1 over split sweeps: returns (x_k, k, relres_k, status) with
+    the same test and counting as ``solve``."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(P.n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    bnorm = float(np.sqrt(np.sum(b * b)))
+    k = 0
+    while True:
+        y, ss, mx = split_sweep(P, b, x)
+        if norm == 2:
+            rel = np.sqrt(ss) / bnorm if bnorm > 0 else np.sqrt(ss)
+        else:
+            rel = mx
+        if rel <= tol:
+            return x, k, float(rel), JO_OK
+        if k == maxit:
+            return x, k, float(rel), JO_ENOTCONV
+        x = y
+        k += 1
 
 
 # ---------------------------------------------------------------------------

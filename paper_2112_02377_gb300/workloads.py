@@ -27,6 +27,10 @@ those files are not available, so these synthetic families stand in for them):
 * ``random_irregular`` -- unstructured diagonally dominant matrix with an
                          irregular row-length mix (a few rows longer than a
                          staged tile), entries in random column order.
+* ``cell_box_locals``  -- the local matrices of substructuring with the
+                         interface block split between subdomains (Sec. 4.3):
+                         each subdomain assembles ``laplace7`` or ``q1_laplace``
+                         from its own box of grid cells only.
 * ``paper_csr_example`` / ``paper_pattern_10x10`` -- the small matrices printed
                          in the paper (Sec. 4.1 CSR example, Sec. 4.2.2 three-band
                          example).
@@ -320,6 +324,110 @@ def q1_laplace(N: int, keep_zeros: bool = False):
             for cc, wx in enumerate(w):
                 bf += wz * wy * wx * f[a:a + g, bb:bb + g, cc:cc + g]
     return A, bf.ravel()
+
+
+# ---------------------------------------------------------------------------
+# Local matrices of substructuring (interface block split between subdomains)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class LocalCSR:
+    """One subdomain's local matrix A_s (Sec. 4.3, Eq. (4.5)): rows and columns
+    are the nodes the subdomain knows, in local numbering, and the entries come
+    from the subdomain's own elements only, so that summed over subdomains
+    they give the assembled matrix; on the interface A33 = sum_s A33^(s)
+    (Eq. (4.6)).  ``l2g[l]`` is the global row of local node l."""
+
+    n: int
+    rowptr: np.ndarray            # int32[n+1]
+    col: np.ndarray               # int32[nnz], local indices
+    val: np.ndarray               # float64[nnz]
+    l2g: np.ndarray               # int32[n]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+
+def _cell_cuts(g: int, p: int):
+    """Cell boxes along one axis of g unknown nodes (indices 0..g-1, Dirichlet
+    ghosts at -1 and g): cell c spans nodes c and c+1, c = -1..g-1, and box t
+    holds cells [cuts[t], cuts[t+1] - 1].  Neighbouring boxes share the node
+    plane cuts[t], t = 1..p-1, which is floor(t g / p): the separator planes
+    of the node-based substructuring."""
+    if p < 1 or p > g:
+        raise ValueError("need 1 <= subdomains per axis <= nodes per axis")
+    return [-1] + [(t * g) // p for t in range(1, p)] + [g]
+
+
+def cell_box_locals(kind: str, m, sub) -> list:
+    """Local matrices of ``laplace7(m)`` (kind "laplace7") or of
+    ``q1_laplace(m)`` (kind "q1", m = nodes per axis including the boundary)
+    split into px*py*pz subdomains of grid cells.
+
+    Both operators are sums of per-cell element matrices over the cells of the
+    grid, Dirichlet ghost cells included:
+      laplace7: 3/4 on the diagonal and -1/4 between the two ends of each of
+                the cell's 12 edges (8 cells give 6, 4 cells give -1);
+      q1:       the trilinear stiffness of a cube of side h = 1/(m-1): h/3 on
+                the diagonal, 0 along an edge, -h/12 across a face or the body
+                diagonal (the zero couplings are not stored).
+    Subdomain s = sx + px (sy + py sz) assembles its own box of cells, so
+    every entry is (element entry) x (number of the box's cells holding both
+    nodes).  Nodes on the shared planes belong to 2, 4 or 8 subdomains.
+    Rows keep their entries in ascending local column order.
+    """
+    if kind == "laplace7":
+        gx, gy, gz = _grid_dims(m)
+        offs = [(dx, dy, dz) for (dx, dy, dz) in _OFF7]
+        coef = {0: 0.75, 1: -0.25}
+    elif kind == "q1":
+        N = int(m)
+        gx = gy = gz = N - 2
+        h = 1.0 / (N - 1)
+        offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                if sum(1 for v in (dx, dy, dz) if v) != 1]
+        coef = {0: h / 3.0, 2: -h / 12.0, 3: -h / 12.0}
+    else:
+        raise ValueError(f"unknown kind {kind!r}")
+    px, py, pz = (int(v) for v in sub)
+    cuts = [_cell_cuts(g, p) for g, p in ((gx, px), (gy, py), (gz, pz))]
+    dims = (gx, gy, gz)
+
+    def axis_count(a, d, clo, chi, g):
+        # cells of [clo, chi] holding node a and node a+d (d in -1, 0, 1) along one axis
+        if d == 0:
+            return (((a - 1 >= clo) & (a - 1 <= chi)).astype(np.int64) + ((a >= clo) & (a <= chi)))
+        c = np.minimum(a, a + d)
+        return ((c >= clo) & (c <= chi) & (a + d >= 0) & (a + d < g)).astype(np.int64)
+
+    out = []
+    for sz in range(pz):
+        for sy in range(py):
+            for sx in range(px):
+                box = (sx, sy, sz)
+                lo = [max(cuts[a][box[a]], 0) for a in range(3)]
+                hi = [min(cuts[a][box[a] + 1], dims[a] - 1) for a in range(3)]
+                ln = [hi[a] - lo[a] + 1 for a in range(3)]
+                coords = [np.arange(lo[a], hi[a] + 1) for a in range(3)]
+                nl = ln[0] * ln[1] * ln[2]
+                cols = np.empty((nl, len(offs)), dtype=np.int64)
+                vals = np.empty((nl, len(offs)), dtype=np.float64)
+                mask = np.empty((nl, len(offs)), dtype=bool)
+                lin = np.arange(nl).reshape(ln[2], ln[1], ln[0])
+                for e, d in enumerate(offs):
+                    cnt = [axis_count(coords[a], d[a], cuts[a][box[a]], cuts[a][box[a] + 1] - 1, dims[a])
+                           for a in range(3)]
+                    c3 = cnt[2][:, None, None] * cnt[1][None, :, None] * cnt[0][None, None, :]
+                    k = coef[sum(1 for v in d if v)]
+                    cols[:, e] = (lin + d[0] + ln[0] * (d[1] + ln[1] * d[2])).ravel()
+                    vals[:, e] = (k * c3).ravel()
+                    mask[:, e] = (c3 > 0).ravel()
+                rowptr, col, val = _rows_to_csr(nl, cols, vals, mask)
+                Z, Y, X = np.meshgrid(coords[2], coords[1], coords[0], indexing="ij")
+                l2g = (X + gx * (Y + gy * Z)).ravel().astype(np.int32)
+                out.append(LocalCSR(nl, rowptr, col, val, l2g))
+    return out
 
 
 # ---------------------------------------------------------------------------
