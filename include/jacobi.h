@@ -152,11 +152,13 @@ typedef struct {
 
 /* Statistics of a context (jac_stats). */
 typedef struct {
-    int64_t n, nnz;               /* rows and stored entries of A (incl. diagonal) */
+    int64_t n, nnz;               /* rows and stored entries of A (incl. diagonal; jac_setup_local:
+                                     of all local matrices) */
     int64_t nparts;               /* partitions of the splitting (SUBSTRUCT: S interiors + 1) */
     int64_t interface_rows;       /* SUBSTRUCT: rows of the interface block */
     int64_t ntiles, ctas;         /* row tiles and CTAs of the sweep kernel */
-    int64_t halo_entries;         /* sum over partitions of received x entries (Sec. 4.2.2) */
+    int64_t halo_entries;         /* sum over partitions of received x entries (Sec. 4.2.2);
+                                     jac_setup_local: interface partial sums assembled per sweep */
     int64_t max_row;              /* longest row (stored entries) */
     int64_t k;                    /* index of the current iterate x^k */
     int64_t sweeps_total;         /* sweeps evaluated since setup / jac_set_x */
@@ -214,6 +216,58 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
  */
 jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const* b,
                              const jac_opts* o, jac_ctx** out);
+
+/* One subdomain's local matrix for jac_setup_local (Sec. 4.3, Eq. (4.5)):
+ * the rows and columns of the nodes the subdomain knows, in local numbering,
+ * with entries assembled from the subdomain's own elements only, so that
+ * A = sum_s P_s^T A_s P_s and on the interface A33 = sum_s A33^(s)
+ * (Eq. (4.6)).  0-based: rowptr has n+1 entries, rowptr[0] == 0,
+ * rowptr[n] == nnz; col holds local indices 0..n-1; l2g[l] is the global row
+ * of local node l (distinct within a subdomain).  A local row holds at most
+ * one diagonal entry (col == l); a missing one counts as 0.  Host memory. */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const double* val;
+    const int32_t* l2g;
+} jac_local;
+
+/*
+ * jac_setup_local -- substructuring with the interface block split between
+ * subdomains (Sec. 4.3): the paper's local matrices, its two-step
+ * matrix-vector product (local products, then the assembly of the partial
+ * interface sums, its collect/send and receive/update algorithms) and its
+ * weighted interface dot product.
+ *   n      global rows; each row 0..n-1 must belong to at least one subdomain.
+ *   nsub   subdomains, 1..65536; sub[s] their local matrices (host memory).
+ *   b      n doubles in the original row order, host memory; NULL = 0.
+ *   o      options (NULL = defaults).  Supported: FP64, nrhs 1, variant 0 or 2,
+ *          tile_rows 0 or 256, sync JAC_SYNC_GRID, ctas_per_sm, lanes_per_row
+ *          (1, 2, 4; 0 = auto), stages, autotune, history, debug, norm.
+ * A row held by one subdomain is interior to it; a row held by m >= 2
+ * subdomains is on the interface (m <= 32 / lanes_per_row).  New row order:
+ * the interiors of subdomains 0..nsub-1 (ascending global row within each),
+ * then the interface (ascending global row).  The assembled diagonal is
+ * d_g = sum_s (A_s)_gg, added in ascending subdomain order, computed once.
+ * A sweep, in the y = D x form of jac_sweep: each subdomain sums its local
+ * off-diagonal terms of each of its rows with S^(s)_gj = -(A_s)_gj / d_j;
+ * an interior row's sum is complete; the partial sums of an interface row
+ * are added to b_g in ascending subdomain order.  Every interface row is
+ * evaluated once, so the residual norm counts it once, which is what the
+ * paper's 1/m weights of the interface dot product achieve.
+ * jac_set_x, jac_set_b, jac_sweep, jac_solve, jac_get_x, jac_get_history,
+ * jac_get_trace and jac_stats work as for jac_setup contexts; jac_stats
+ * reports nnz = stored entries of all local matrices, nparts = nsub + 1 and
+ * halo_entries = interface partial sums assembled per sweep.
+ * Errors: JAC_EINVAL (sizes, indices, a row in no subdomain, a repeated l2g
+ * within a subdomain, two diagonal entries in a local row, too many
+ * subdomains on one row for the lane count, an unsupported option),
+ * JAC_ESINGULAR (an assembled diagonal entry is 0), JAC_ENOMEM, JAC_ECUDA.
+ */
+jac_status jac_setup_local(int64_t n, int32_t nsub, const jac_local* sub, const double* b,
+                           const jac_opts* o, jac_ctx** out);
 
 /*
  * jac_set_x -- set the current iterate x^0 (warm start / resume; Algorithm 1

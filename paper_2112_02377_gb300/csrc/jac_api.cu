@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +32,12 @@ struct jac_ctx {
     jac_opts o{};
     std::string err = "no error";
     int64_t n = 0, nnz = 0, nnz_off = 0, max_row = 0, max_off = 0, halo_entries = 0, interface_rows = 0;
+    int64_t rows = 0;              // kernel rows (n, or more with a split interface block)
+    // split interface block (jac_setup_local): rows at and after n_own are slot rows
+    bool split = false;
+    int64_t n_own = 0;
+    long long* d_bmap = nullptr;   // rows: original row whose b starts each kernel row's sum, -1 = none
+    unsigned* d_slot_info = nullptr;
     int nrhs = 1;
     int splitting = 0, precision = 0, variant = 2;
     int64_t nparts = 0;
@@ -211,6 +219,8 @@ DevMat devmat(const jac_ctx* c)
     m.S32 = c->d_S32;
     m.b = c->d_b;
     m.d = c->d_d;
+    m.n_own = (int)(c->split ? c->n_own : c->n);
+    m.slot_info = c->d_slot_info;
     return m;
 }
 
@@ -452,6 +462,7 @@ void destroy(jac_ctx* c)
     dfree(c->d_x[0]); dfree(c->d_x[1]); dfree(c->d_x[2]);
     dfree(c->d_dep_ptr); dfree(c->d_dep); dfree(c->d_done); dfree(c->d_e[0]); dfree(c->d_e[1]); dfree(c->d_dlt);
     dfree(c->d_part); dfree(c->d_ctl); dfree(c->d_hist); dfree(c->d_perm); dfree(c->d_stage); dfree(c->d_stage2);
+    dfree(c->d_bmap); dfree(c->d_slot_info);
     dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0);
     dfree(c->d_row1); dfree(c->d_nnz1); dfree(c->d_cta0);
     dfree(c->d_blk0); dfree(c->d_blk); dfree(c->d_lcol); dfree(c->d_trace);
@@ -739,56 +750,39 @@ jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t npart
 
 inline int64_t nnz_off_of(const ScaledForm& tf) { return tf.rowptr.empty() ? 0 : tf.rowptr.back(); }
 
-// One context with fixed options; row_cost (NULL: the default model) sets
-// how the persistent variants cut the CTA row ranges.
-static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, jac_opts o,
-                               const std::vector<double>* row_cost, jac_ctx** out)
+// A context from a matrix already split and scaled: tf holds the kernel rows
+// (tf.n of them; n for jac_setup, more with a split interface block), tf.d and
+// the iterate the n rows.  sp: the split interface layout (jac_setup_local),
+// else NULL.  pattern: the caller's CSR pattern for the adjoint gradient
+// (forward jac_setup contexts), else NULL.  b: n doubles in b_memory.
+// row_cost (NULL: the default model) sets how the persistent variants cut
+// the CTA row ranges.
+static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, int64_t nnz, int64_t halo_entries,
+                             const SplitForm* sp, const HostCSR* pattern, const double* b, int32_t b_memory,
+                             jac_opts o, int dev, const std::vector<double>* row_cost, jac_ctx** out)
 {
-    *out = nullptr;
-    if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
-    jac_status st = check_opts(o, nullptr);
-    if (st != JAC_OK) return st;
-    int dev = o.device;
-    if (dev < 0) {
-        if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, JAC_ECUDA, "no CUDA device");
-    }
-    DeviceGuard guard(dev);
-    HostView hv;
-    st = host_view(A, hv, nullptr);
-    if (st != JAC_OK) return st;
-    HostCSR M;
-    Error e = host_csr_from_abi(&hv.csr, o.transpose != 0, M);
-    if (!e.ok()) return fail(nullptr, e.st, e.msg);
-    Plan plan;
-    e = make_plan(M, s, nparts, o, plan);
-    if (!e.ok()) return fail(nullptr, e.st, e.msg);
-    ScaledForm tf;
-    e = make_scaled_form(M, plan, tf);
-    if (!e.ok()) return fail(nullptr, e.st, e.msg);
-
+    jac_status st = JAC_OK;
     std::unique_ptr<jac_ctx, void (*)(jac_ctx*)> c(new jac_ctx(), destroy);
     c->device = dev;
     c->stream = (cudaStream_t)o.stream;
     c->o = o;
-    c->n = M.n;
-    c->nnz = M.nnz();
-    c->nnz_off = tf.rowptr[M.n];
+    c->n = n;
+    c->rows = tf.n;
+    c->split = sp != nullptr;
+    c->n_own = sp ? sp->n_own : n;
+    c->nnz = nnz;
+    c->nnz_off = tf.rowptr[tf.n];
     c->max_off = tf.max_off;
     c->max_row = tf.max_off + 1;
-    c->splitting = s;
+    c->splitting = plan.splitting;
     c->precision = o.precision;
     c->nparts = plan.nparts();
     c->interface_rows = plan.interface_rows;
     c->K = o.sweeps_per_graph;
-    {
-        std::vector<int64_t> rp, rc;
-        std::vector<int32_t> rf;
-        dependency_lists(M, plan, rp, rf, rc);
-        c->halo_entries = (int64_t)rc.size();
-    }
+    c->halo_entries = halo_entries;
     jac_ctx* C = c.get();
-    const int64_t n = M.n, nnz_off = c->nnz_off;
-    if (n > INT32_MAX - 64) return fail(nullptr, JAC_EINVAL, "n too large");
+    const int64_t rows = tf.n, nnz_off = c->nnz_off;
+    if (rows > INT32_MAX - 64) return fail(nullptr, JAC_EINVAL, "n too large");
 
     // ---- launch configuration
     cudaDeviceProp prop;
@@ -815,7 +809,7 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     // best with L = 2, 7-point rows with L = 1).
     c->lanes = 1;
     if (c->variant == 2 && c->rows_per_tile == 256) {
-        const double avg = n > 0 ? (double)nnz_off_of(tf) / (double)n : 0.0;
+        const double avg = rows > 0 ? (double)nnz_off_of(tf) / (double)rows : 0.0;
         if (o.lanes_per_row) c->lanes = o.lanes_per_row;
         else while (c->lanes < 8 && avg / (2.0 * c->lanes) >= 8.0) c->lanes *= 2;
     } else if (o.lanes_per_row > 1) {
@@ -846,24 +840,28 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
         } else {
             c->sync = (c->variant == 2 && c->rows_per_tile == 256) ? o.sync : JAC_SYNC_GRID;
             c->ns = c->sync == JAC_SYNC_NEIGHBOUR;
-            c->pfn64 = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, c->sync);
-            c->pfn64grid = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, JAC_SYNC_GRID);
-            c->pfnmix = persistent_kernel(c->rows_per_tile, c->stages, true, c->lanes, false);
+            // kernel form 3: the grid-synchronised FP64 kernel over a split interface layout
+            const int form = sp ? 3 : c->sync;
+            c->pfn64 = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, form);
+            c->pfn64grid = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, sp ? 3 : JAC_SYNC_GRID);
+            // split layouts are FP64 only: no mixed kernel
+            c->pfnmix = sp ? nullptr : persistent_kernel(c->rows_per_tile, c->stages, true, c->lanes, false);
             c->smem = persistent_smem_bytes(rows, c->emax, c->stages);
         }
         c->threads = (c->variant == 3) ? 256 + 32 : persistent_threads(c->rows_per_tile);
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         auto occupancy = [&](int smem_bytes) -> int {
-            if (!c->pfn64 || !c->pfnmix) return 0;
+            if (!c->pfn64 || (!c->pfnmix && !sp)) return 0;
+            const void* fmix = c->pfnmix ? c->pfnmix : c->pfn64;
             if (cudaFuncSetAttribute(c->pfn64, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess ||
-                cudaFuncSetAttribute(c->pfnmix, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess) {
+                cudaFuncSetAttribute(fmix, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess) {
                 cudaGetLastError();
                 return 0;
             }
             int a = 0, b2 = 0, a3 = 1 << 20;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, c->pfn64, c->threads, smem_bytes) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, c->pfnmix, c->threads, smem_bytes) != cudaSuccess) {
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, fmix, c->threads, smem_bytes) != cudaSuccess) {
                 cudaGetLastError();
                 return 0;
             }
@@ -921,14 +919,16 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
         c->grid = (int)((n + 255) / 256);
         c->emax = 0;
     }
-    if (c->variant == 2) make_tiling(tf, plan, c->rows_per_tile / c->lanes, c->emax, c->grid, tl, row_cost);
+    if (c->variant == 2)
+        make_tiling(tf, plan, c->rows_per_tile / c->lanes, c->emax, c->grid, tl, row_cost,
+                    sp ? sp->n_own : INT64_MAX, sp ? sp->warp_rows : 1);
     if (c->variant >= 2) {
         c->ntiles = (int)tl.ntiles();
         // what the balance calibration needs: each CTA's rows and the cost model used
         c->h_cta_row0.resize(c->grid + 1);
         for (int g = 0; g <= c->grid; ++g) c->h_cta_row0[g] = tl.row0[tl.cta0[g]];
-        c->h_row_cost.resize(n);
-        for (int64_t r = 0; r < n; ++r)
+        c->h_row_cost.resize(rows);
+        for (int64_t r = 0; r < rows; ++r)
             c->h_row_cost[r] = row_cost ? (*row_cost)[r] : default_row_cost(tf.rowptr[r + 1] - tf.rowptr[r]);
     }
     std::vector<int32_t> dep_ptr, dep;
@@ -936,7 +936,7 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
         // each CTA's neighbours: the CTAs that own a row it reads (Sec. 4.2.2's
         // dependency lists at CTA granularity)
         const int G = c->grid;
-        std::vector<int32_t> cta_of(n);
+        std::vector<int32_t> cta_of(rows);
         for (int g = 0; g < G; ++g)
             for (int64_t r = c->h_cta_row0[g]; r < c->h_cta_row0[g + 1]; ++r) cta_of[r] = g;
         std::vector<int32_t> stamp(G, -1);
@@ -957,10 +957,18 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     c->nslots = c->grid;
 
     // ---- device buffers
-    CK(nullptr, dalloc(&c->d_rowptr, n + 1 + 16));
+    CK(nullptr, dalloc(&c->d_rowptr, rows + 1 + 16));
     CK(nullptr, dalloc(&c->d_col, nnz_off + 16));
     CK(nullptr, dalloc(&c->d_S64, nnz_off + 16));
-    CK(nullptr, dalloc(&c->d_b, n + 16));
+    CK(nullptr, dalloc(&c->d_b, rows + 16));
+    if (sp) {
+        CK(nullptr, dalloc(&c->d_bmap, rows + 16));
+        CK(nullptr, dalloc(&c->d_slot_info, sp->slot_info.size() + 16));
+        CK(nullptr, cudaMemcpy(c->d_bmap, sp->bmap.data(), rows * sizeof(long long), cudaMemcpyHostToDevice));
+        if (!sp->slot_info.empty())
+            CK(nullptr, cudaMemcpy(c->d_slot_info, sp->slot_info.data(), sp->slot_info.size() * 4,
+                                   cudaMemcpyHostToDevice));
+    }
     CK(nullptr, dalloc(&c->d_d, n + 16));
     CK(nullptr, dalloc(&c->d_x[0], n + 16));
     CK(nullptr, dalloc(&c->d_x[1], n + 16));
@@ -1014,7 +1022,7 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
         CK(nullptr, cudaMemcpy(c->d_nnz0, tl.nnz0.data(), tl.nnz0.size() * 4, cudaMemcpyHostToDevice));
         CK(nullptr, cudaMemcpy(c->d_cta0, tl.cta0.data(), tl.cta0.size() * 4, cudaMemcpyHostToDevice));
     }
-    CK(nullptr, cudaMemcpy(c->d_rowptr, tf.rowptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
+    CK(nullptr, cudaMemcpy(c->d_rowptr, tf.rowptr.data(), (rows + 1) * 4, cudaMemcpyHostToDevice));
     if (nnz_off) {
         CK(nullptr, cudaMemcpy(c->d_col, tf.col.data(), nnz_off * 4, cudaMemcpyHostToDevice));
         CK(nullptr, cudaMemcpy(c->d_S64, tf.S.data(), nnz_off * 8, cudaMemcpyHostToDevice));
@@ -1028,10 +1036,8 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     c->h_perm.assign(plan.perm.begin(), plan.perm.end());
     CK(nullptr, cudaMemcpy(c->d_perm, c->h_perm.data(), n * sizeof(long long), cudaMemcpyHostToDevice));
     // original pattern for the adjoint gradient (forward contexts)
-    if (!o.transpose) {
-        HostCSR P;
-        Error e2 = host_csr_from_abi(&hv.csr, false, P);
-        if (!e2.ok()) return fail(nullptr, e2.st, e2.msg);
+    if (pattern) {
+        const HostCSR& P = *pattern;
         CK(nullptr, dalloc(&c->d_orow, n + 1));
         CK(nullptr, dalloc(&c->d_ocol, (size_t)P.nnz()));
         CK(nullptr, cudaMemcpy(c->d_orow, P.rowptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
@@ -1039,11 +1045,15 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     }
     if (o.debug) {
         const size_t nn = (size_t)n;
-        add_canary(C, "rowptr", c->d_rowptr, nn + 1);
+        add_canary(C, "rowptr", c->d_rowptr, (size_t)rows + 1);
         add_canary(C, "col", c->d_col, (size_t)nnz_off);
         add_canary(C, "S64", c->d_S64, (size_t)nnz_off);
         add_canary(C, "S32", c->d_S32, (size_t)nnz_off);
-        add_canary(C, "b", c->d_b, nn);
+        add_canary(C, "b", c->d_b, (size_t)rows);
+        if (sp) {
+            add_canary(C, "bmap", c->d_bmap, (size_t)rows);
+            add_canary(C, "slot_info", c->d_slot_info, sp->slot_info.size());
+        }
         add_canary(C, "d", c->d_d, nn);
         add_canary(C, "x[0]", c->d_x[0], nn);
         add_canary(C, "x[1]", c->d_x[1], nn);
@@ -1058,10 +1068,11 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     // right-hand side and control block
     cudaStream_t sm = stream_of(C);
     if (b) {
-        st = copy_to_stage(C, b, A->memory, (size_t)n, c->d_stage);
+        st = copy_to_stage(C, b, b_memory, (size_t)n, c->d_stage);
         if (st != JAC_OK) return fail(nullptr, st, C->err);
     }
-    CK(nullptr, launch_gather_b(c->d_perm, b ? c->d_stage : nullptr, c->d_b, (int)n, c->d_ctl, sm));
+    CK(nullptr, launch_gather_b(sp ? c->d_bmap : c->d_perm, b ? c->d_stage : nullptr, c->d_b, (int)rows, (int)n,
+                                c->d_ctl, sm));
     CK(nullptr, launch_reset_iterate(c->d_ctl, sm));
     CK(nullptr, launch_arm(c->d_ctl, 0, 0, o.inner_sweeps, 0, 0, -1.0, o.norm, c->d_hist, c->hist_cap, (long long)o.timeout_cycles,
                      o.fault_skip_cta, sm));
@@ -1071,6 +1082,110 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     return JAC_OK;
 }
 
+
+// One context with fixed options from a CSR matrix.
+static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, jac_opts o,
+                               const std::vector<double>* row_cost, jac_ctx** out)
+{
+    *out = nullptr;
+    if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
+    jac_status st = check_opts(o, nullptr);
+    if (st != JAC_OK) return st;
+    int dev = o.device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, JAC_ECUDA, "no CUDA device");
+    }
+    DeviceGuard guard(dev);
+    HostView hv;
+    st = host_view(A, hv, nullptr);
+    if (st != JAC_OK) return st;
+    HostCSR M;
+    Error e = host_csr_from_abi(&hv.csr, o.transpose != 0, M);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    Plan plan;
+    e = make_plan(M, s, nparts, o, plan);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    ScaledForm tf;
+    e = make_scaled_form(M, plan, tf);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    std::vector<int64_t> rp, rc;
+    std::vector<int32_t> rf;
+    dependency_lists(M, plan, rp, rf, rc);
+    // without transpose, M is the caller's pattern (the adjoint gradient's)
+    return setup_core(plan, tf, M.n, M.nnz(), (int64_t)rc.size(), nullptr, o.transpose ? nullptr : &M, b,
+                      A->memory, o, dev, row_cost, out);
+}
+
+// Autotuner: set up every candidate geometry with `make`, time a few sweeps
+// of each on this matrix and keep the fastest; then re-cut its CTA row ranges
+// from the measured per-CTA compute times while that keeps paying.
+using MakeCtx = std::function<jac_status(const jac_opts&, const std::vector<double>*, jac_ctx**)>;
+static jac_status tune(const jac_opts& o, const std::vector<Geometry>& cand, const MakeCtx& make, jac_ctx** out)
+{
+    const bool async = (o.sync == JAC_SYNC_ASYNC);
+    jac_ctx* best = nullptr;
+    jac_opts best_o = o;
+    double best_ms = 1e30;
+    std::string first_err;
+    for (const Geometry& g : cand) {
+        jac_opts o2 = o;
+        o2.autotune = 0;
+        o2.variant = g.variant;
+        o2.tile_rows = g.rows;
+        o2.ctas_per_sm = g.ctas;
+        if (g.lanes) o2.lanes_per_row = g.lanes;
+        o2.stages = g.stages;
+        o2.sync = async ? JAC_SYNC_ASYNC : g.sync;
+        jac_ctx* c = nullptr;
+        const jac_status st = make(o2, nullptr, &c);
+        if (st != JAC_OK) {
+            if (first_err.empty()) first_err = g_setup_error;
+            if (st != JAC_EINVAL) return st;   // invalid matrix etc.: no geometry will do
+            continue;
+        }
+        const double ms = time_per_sweep(c);
+        if (ms < best_ms) {
+            if (best) jac_free(best);
+            best = c;
+            best_o = o2;
+            best_ms = ms;
+        } else {
+            jac_free(c);
+        }
+    }
+    if (!best) return fail(nullptr, JAC_EINVAL, "autotune: no kernel geometry could be set up: " + first_err);
+    // Balance calibration: the sweep waits for the slowest CTA, so scale the
+    // cost estimate of every row by its CTA's measured time per unit of
+    // estimated cost and cut the ranges again.
+    for (int it = 0; it < 3 && best->variant >= 2 && best->n > 0; ++it) {
+        const int G = best->grid;
+        std::vector<double> comp(G, 0.0);
+        int64_t nct = 0;
+        if (jac_get_trace(best, comp.data(), nullptr, G, &nct) != JAC_OK || nct != G) break;
+        std::vector<double> w = best->h_row_cost;
+        for (int g = 0; g < G; ++g) {
+            const int64_t r0 = best->h_cta_row0[g], r1 = best->h_cta_row0[g + 1];
+            double W = 0.0;
+            for (int64_t r = r0; r < r1; ++r) W += w[r];
+            if (W <= 0.0 || !(comp[g] > 0.0)) continue;
+            const double f = comp[g] / W;
+            for (int64_t r = r0; r < r1; ++r) w[r] *= f;
+        }
+        jac_ctx* c = nullptr;
+        if (make(best_o, &w, &c) != JAC_OK) break;
+        const double ms = time_per_sweep(c);
+        if (ms < best_ms) {
+            jac_free(best);
+            best = c;
+            best_ms = ms;
+        } else {
+            jac_free(c);
+            break;
+        }
+    }
+    *out = best;
+    return JAC_OK;
+}
 
 jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, const jac_opts* o_in,
                      jac_ctx** out)
@@ -1122,68 +1237,91 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
                     }
         }
     }
-    jac_ctx* best = nullptr;
-    jac_opts best_o = o;
-    double best_ms = 1e30;
-    std::string first_err;
-    for (const Geometry& g : cand) {
-        jac_opts o2 = o;
-        o2.autotune = 0;
-        o2.variant = g.variant;
-        o2.tile_rows = g.rows;
-        o2.ctas_per_sm = g.ctas;
-        if (g.lanes) o2.lanes_per_row = g.lanes;
-        o2.stages = g.stages;
-        o2.sync = async ? JAC_SYNC_ASYNC : g.sync;
-        jac_ctx* c = nullptr;
-        const jac_status st = setup_single(A, b, s, nparts, o2, nullptr, &c);
-        if (st != JAC_OK) {
-            if (first_err.empty()) first_err = g_setup_error;
-            if (st != JAC_EINVAL) return st;   // invalid matrix etc.: no geometry will do
-            continue;
+    return tune(o, cand, [&](const jac_opts& oc, const std::vector<double>* rc, jac_ctx** pc) {
+        return setup_single(A, b, s, nparts, oc, rc, pc);
+    }, out);
+}
+
+jac_status jac_setup_local(int64_t n, int32_t nsub, const jac_local* sub, const double* b, const jac_opts* o_in,
+                           jac_ctx** out)
+{
+    if (!out) return fail(nullptr, JAC_EINVAL, "out is NULL");
+    *out = nullptr;
+    jac_opts o;
+    jac_opts_default(&o);
+    if (o_in) o = *o_in;
+    if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
+    jac_status st = check_opts(o, nullptr);
+    if (st != JAC_OK) return st;
+    if (o.precision != JAC_FP64 || o.nrhs != 1 || o.transpose || (o.variant != 0 && o.variant != 2) ||
+        (o.tile_rows != 0 && o.tile_rows != 256) || o.sync != JAC_SYNC_GRID || o.lanes_per_row > 4)
+        return fail(nullptr, JAC_EINVAL,
+                    "jac_setup_local: FP64, nrhs 1, no transpose, variant 0/2 with 256-thread tiles, grid sync and "
+                    "lanes_per_row <= 4 only");
+    if (o.autotune && o.ctas_per_sm)
+        return fail(nullptr, JAC_EINVAL, "autotune needs ctas_per_sm = 0");
+    // Lane counts a row's subdomains fit (one warp of 32 / L rows holds them all).
+    const int32_t mmax = split_max_multiplicity(n, nsub, sub);
+    std::vector<int> lanes_ok;
+    for (int L : {1, 2, 4})
+        if (mmax == 0 || mmax <= 32 / L) lanes_ok.push_back(L);
+    // automatic lane count: jac_setup's rule on the average local row, capped by the above
+    int auto_lanes = 1;
+    {
+        double rows = 0.0, ent = 0.0;
+        for (int32_t s2 = 0; sub && s2 < nsub; ++s2) {
+            rows += std::max(0, sub[s2].n);
+            ent += (double)std::max<int64_t>(0, sub[s2].nnz) - std::max(0, sub[s2].n);
         }
-        const double ms = time_per_sweep(c);
-        if (ms < best_ms) {
-            if (best) jac_free(best);
-            best = c;
-            best_o = o2;
-            best_ms = ms;
-        } else {
-            jac_free(c);
+        const double avg = rows > 0 ? ent / rows : 0.0;
+        while (auto_lanes < 4 && avg / (2.0 * auto_lanes) >= 8.0) auto_lanes *= 2;
+        while (auto_lanes > 1 && std::find(lanes_ok.begin(), lanes_ok.end(), auto_lanes) == lanes_ok.end())
+            auto_lanes /= 2;
+    }
+    // validate everything on the host before the first CUDA call
+    std::map<int, SplitForm> forms;
+    auto form_for = [&](int L, const SplitForm** f) -> jac_status {
+        auto it = forms.find(L);
+        if (it == forms.end()) {
+            SplitForm sf;
+            Error e = make_split_form(n, nsub, sub, 32 / L, sf);
+            if (!e.ok()) return fail(nullptr, e.st, e.msg);
+            it = forms.emplace(L, std::move(sf)).first;
+        }
+        *f = &it->second;
+        return JAC_OK;
+    };
+    const int L0 = o.lanes_per_row ? o.lanes_per_row : auto_lanes;
+    const SplitForm* f0 = nullptr;
+    st = form_for(L0, &f0);
+    if (st != JAC_OK) return st;
+    int dev = o.device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, JAC_ECUDA, "no CUDA device");
+    }
+    DeviceGuard guard(dev);
+    auto make = [&](const jac_opts& oc, const std::vector<double>* rc, jac_ctx** pc) -> jac_status {
+        jac_opts o2 = oc;
+        o2.variant = 2;
+        o2.tile_rows = 256;
+        if (!o2.lanes_per_row) o2.lanes_per_row = L0;
+        const SplitForm* f = nullptr;
+        const jac_status s2 = form_for(o2.lanes_per_row, &f);
+        if (s2 != JAC_OK) return s2;
+        return setup_core(f->plan, f->tf, n, f->nnz_local, f->partials, f, nullptr, b, JAC_MEM_HOST, o2, dev, rc, pc);
+    };
+    if (!o.autotune) return make(o, nullptr, out);
+    std::vector<Geometry> cand;
+    for (int L : lanes_ok) {
+        if (o.lanes_per_row && L != o.lanes_per_row) continue;
+        cand.push_back({2, 256, 2, L});
+        cand.push_back({2, 256, 3, L});
+        if (L >= 2) {
+            cand.push_back({2, 256, 2, L, JAC_SYNC_GRID, 3});
+            cand.push_back({2, 256, 2, L, JAC_SYNC_GRID, 2});
         }
     }
-    if (!best) return fail(nullptr, JAC_EINVAL, "autotune: no kernel geometry could be set up: " + first_err);
-    // Balance calibration: the sweep waits for the slowest CTA, so scale the
-    // cost estimate of every row by its CTA's measured time per unit of
-    // estimated cost and cut the ranges again.
-    for (int it = 0; it < 3 && best->variant >= 2 && best->n > 0; ++it) {
-        const int G = best->grid;
-        std::vector<double> comp(G, 0.0);
-        int64_t nct = 0;
-        if (jac_get_trace(best, comp.data(), nullptr, G, &nct) != JAC_OK || nct != G) break;
-        std::vector<double> w = best->h_row_cost;
-        for (int g = 0; g < G; ++g) {
-            const int64_t r0 = best->h_cta_row0[g], r1 = best->h_cta_row0[g + 1];
-            double W = 0.0;
-            for (int64_t r = r0; r < r1; ++r) W += w[r];
-            if (W <= 0.0 || !(comp[g] > 0.0)) continue;
-            const double f = comp[g] / W;
-            for (int64_t r = r0; r < r1; ++r) w[r] *= f;
-        }
-        jac_ctx* c = nullptr;
-        if (setup_single(A, b, s, nparts, best_o, &w, &c) != JAC_OK) break;
-        const double ms = time_per_sweep(c);
-        if (ms < best_ms) {
-            jac_free(best);
-            best = c;
-            best_ms = ms;
-        } else {
-            jac_free(c);
-            break;
-        }
-    }
-    *out = best;
-    return JAC_OK;
+    return tune(o, cand, make, out);
 }
 
 jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const* b, const jac_opts* o_in,
@@ -1283,6 +1421,7 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     c->nsys = nsys;
     c->nrhs = nrhs;
     c->n = n;
+    c->rows = n;
     c->nnz = nnz_off + n;
     c->nnz_off = nnz_off;
     c->max_off = big.max_off;
@@ -1457,7 +1596,8 @@ jac_status jac_set_b(jac_ctx* c, const double* b, int32_t memory)
         jac_status st = copy_to_stage(c, b, memory, (size_t)c->n, c->d_stage);
         if (st != JAC_OK) return st;
     }
-    CK(c, launch_gather_b(c->d_perm, b ? c->d_stage : nullptr, c->d_b, (int)c->n, c->d_ctl, s));
+    CK(c, launch_gather_b(c->split ? c->d_bmap : c->d_perm, b ? c->d_stage : nullptr, c->d_b, (int)c->rows,
+                          (int)c->n, c->d_ctl, s));
     CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
     return JAC_OK;
 }

@@ -74,6 +74,12 @@ struct DevMat {
     const float* S32;         // nnz_off (+pad), mixed only
     const double* b;          // n (+pad): right-hand side in the new order
     const double* d;          // n (+pad): a_ii (conversions x <-> y only)
+    // Split interface block (Sec. 4.3 local matrices): kernel rows at and after
+    // n_own are slot rows holding partial sums of interface rows (n_own == n
+    // and slot_info == NULL otherwise).  rowptr/col/S64/b then cover the
+    // kernel rows; d and the iterate the n rows.
+    int n_own;
+    const unsigned* slot_info;   // per slot row: (interface index << 6) | group size at a group's first row
 };
 
 struct DevVec {

@@ -72,6 +72,24 @@ struct Windows {
 };
 enum : int32_t { TILE_FALLBACK = 1 };   // tile reads x from L2 with global columns
 
+// Substructuring with the interface block split between subdomains (Sec.
+// 4.3), laid out for the persistent kernel.  Kernel rows: the n_own interior
+// rows first (row r is iterate entry r), then "slot rows": one per (interface
+// row g, subdomain s holding g), carrying the off-diagonal entries of
+// (A_s)_g.  The slot rows of one interface row are consecutive, in ascending
+// subdomain order, and never straddle a multiple of warp_rows (counted from
+// n_own; padding rows are empty), so one warp holds all of them; the first
+// one starts from b_g and its lane adds the others' sums in order.
+struct SplitForm {
+    ScaledForm tf;                      // tf.n = kernel rows; tf.d has the n assembled diagonals
+    Plan plan;                          // perm/iperm over the n rows; part_ptr over kernel rows
+    int64_t n = 0, n_own = 0, n_ifc = 0, nnz_local = 0, partials = 0;
+    int32_t warp_rows = 32, max_mult = 1;
+    std::vector<uint32_t> slot_info;    // per slot row: (interface index << 6) | group size at a
+                                        // group's first row, 0 elsewhere
+    std::vector<int64_t> bmap;          // per kernel row: original row whose b starts the sum, -1 = none
+};
+
 struct Error {
     jac_status st = JAC_OK;
     std::string msg;
@@ -88,8 +106,14 @@ void dependency_lists(const HostCSR& A, const Plan& plan, std::vector<int64_t>& 
                       std::vector<int32_t>& recv_from, std::vector<int64_t>& recv);
 // row_cost: per-row cost estimates in the new order (NULL: default_row_cost).
 double default_row_cost(int64_t off_entries);
+// Rows at and after align_from are cut only at align_from + multiples of align.
 void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
-                 int64_t ctas, Tiling& t, const std::vector<double>* row_cost = nullptr);
+                 int64_t ctas, Tiling& t, const std::vector<double>* row_cost = nullptr,
+                 int64_t align_from = INT64_MAX, int32_t align = 1);
+// Validates the local matrices and builds the split layout for lanes = 32 / warp_rows.
+Error make_split_form(int64_t n, int32_t nsub, const jac_local* sub, int32_t warp_rows, SplitForm& out);
+// Largest number of subdomains holding one row (0 if the input is malformed).
+int32_t split_max_multiplicity(int64_t n, int32_t nsub, const jac_local* sub);
 HostCSR transpose_csr(const HostCSR& A);
 void make_windows(const ScaledForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w);
 

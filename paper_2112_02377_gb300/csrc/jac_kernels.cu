@@ -128,6 +128,36 @@ __device__ __noinline__ Real lanes_global(const Real* S, const int* col, const R
     return acc;
 }
 
+// Interface rows of a split interface block (Sec. 4.3, the two-step product):
+// a warp's slot rows hold whole groups, one group per interface row g, its
+// rows consecutive in ascending subdomain order, each the partial sum of one
+// subdomain's local row; the first row's sum started from b_g.  The lane of
+// that first row (info = (interface index << 6) | group size, 0 elsewhere)
+// adds the other rows' sums in order -- the receive/update step -- stores y'_g
+// and returns (y'_g, y_g); other lanes return zeros.  All 32 lanes call it
+// (the acc of a row is the same on its L lanes after group_sum).
+template <int L>
+__device__ __noinline__ double2 split_assemble(double acc, unsigned info, int n_own, const double* xs, double* xd)
+{
+    const int lane = threadIdx.x & 31;
+    const int g = (int)(info & 63u);
+    const int gmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)g);
+    double y = acc;
+    for (int q = 1; q < gmax; ++q) {
+        const int src = lane + q * L;
+        const double v = __shfl_sync(0xffffffffu, acc, src < 32 ? src : 31);
+        if (q < g) y = __dadd_rn(y, v);
+    }
+    double2 out = make_double2(0.0, 0.0);
+    if (g) {
+        const int gi = n_own + (int)(info >> 6);
+        out.x = y;
+        out.y = __ldcg(xs + gi);
+        __stcg(xd + gi, y);
+    }
+    return out;
+}
+
 // Entries prefetched per row by the pipelined persistent kernel (a 7-point row
 // has 6 off-diagonal entries); longer rows finish in row_tail.
 constexpr int PF = 6;
@@ -325,7 +355,8 @@ __device__ __forceinline__ void consumer_sync()
 // LPR = lanes per row: a tile holds 256/LPR rows, each summed by LPR lanes.
 //
 // SYNC orders consecutive sweeps: 0 = grid barrier, 1 = neighbour flags, 2 =
-// none (asynchronous relaxation, see below).
+// none (asynchronous relaxation, see below), 3 = grid barrier over a split
+// interface layout (rows from n_own on are slot rows, see split_assemble).
 //
 // SYNC = 1, neighbour-synchronised FP64 sweeps.  Instead of a grid barrier after
 // every sweep, a CTA starts sweep j once (a) the CTAs that own the rows it
@@ -350,6 +381,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
 {
     constexpr bool NS = (SYNC == 1);      // neighbour-synchronised sweeps
     constexpr bool ASYNC = (SYNC == 2);   // asynchronous (chaotic) relaxation
+    constexpr bool SPLIT = (SYNC == 3);   // grid barrier; rows from n_own on are slot rows of a split interface
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int CT = NWM * 32, NW = NWM, ROWS = CT * RPT / LPR;
     // 7 or 15 math warps have 128 registers: software-pipeline the x gathers of
@@ -359,6 +391,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     static_assert(!PIPE || LPR == 1, "the pipelined loop sums a row in one lane");
     static_assert(!NS || (!MIXED && !PIPE), "neighbour sync is built for the plain FP64 loop");
     static_assert(!ASYNC || (!MIXED && !PIPE), "asynchronous relaxation is built for the plain FP64 loop");
+    static_assert(!SPLIT || (!MIXED && !PIPE), "the split interface block is built for the plain FP64 loop");
     const StageLayout L = stage_layout(ROWS, t.emax);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes);
     uint64_t* empty = full + STAGES;
@@ -383,8 +416,10 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         s_test = c->test;
         s_done = c->done;
         s_skip = c->fault_skip_cta;
-        // the stages and their barriers must fit the dynamic shared memory of the launch
-        const bool fits = (unsigned long long)STAGES * L.bytes + 2ull * STAGES * 8 <= dynamic_smem_bytes();
+        // the stages and their barriers must fit the dynamic shared memory of the
+        // launch, and a split interface layout needs the kernel form built for it
+        const bool fits = (unsigned long long)STAGES * L.bytes + 2ull * STAGES * 8 <= dynamic_smem_bytes() &&
+                          (m.slot_info != nullptr) == SPLIT;
         if (!fits) atomicOr(&ctl->status, ST_CONFIG);
         s_start = fits && (c->done == DONE_RUNNING) && (c->status == 0);
         s_relres = c->relres;
@@ -687,7 +722,10 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         } else {
             for (int i = 0; i < nt; ++i, ++jc) {
                 const int sidx = (int)(jc % STAGES);
-                const bool ok = wait_full(jc);
+                bool ok = wait_full(jc);
+                // the tile body shuffles across the warp (row groups, interface
+                // groups): after a timeout every lane must skip it together
+                if constexpr (SPLIT || LPR > 1) ok = __all_sync(0xffffffffu, ok);
                 if (ok) {
                     const unsigned char* st = smem + sidx * L.bytes;
                     const int* hdr = reinterpret_cast<const int*>(st);
@@ -699,12 +737,13 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                     const int r = r0 + tid / LPR;
                     const bool in = r < r1;
                     const bool lead = in && q == 0;       // the lane that owns the row's result
+                    const bool own = !SPLIT || r < m.n_own;   // else a slot row of a split interface block
                     const int kb = in ? srp[r] : 0;
                     const int len = in ? srp[r + 1] - kb : 0;
                     if (norm_ph) {
                         const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
                         const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
-                        const double xi = lead ? __ldcg(xs + r) : 0.0;
+                        const double xi = (lead && own) ? __ldcg(xs + r) : 0.0;
                         double acc = lead ? sc[r] : 0.0;
                         if (!over)
                             acc = lanes_dot<LPR>(acc, kb, len, q, [&](int e) { return sv[e]; },
@@ -712,7 +751,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                         else if (in)
                             acc = lanes_global<LPR>(m.S64, m.col, xs, kb, len, q, acc);
                         acc = group_sum<LPR>(acc);
-                        if (lead) {
+                        if (lead && own) {
                             if (ph == PH_P64) {
                                 __stcg(xd + r, acc);
                             } else {
@@ -721,6 +760,13 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                                 __stcg(v.e[1] + r, dl);
                             }
                             accumulate_residual(acc, xi, ss, mx);
+                        }
+                        if constexpr (SPLIT) {
+                            if (r0 >= m.n_own) {          // a tile of slot rows (tiles never mix the two)
+                                const unsigned info = lead ? __ldg(m.slot_info + (r - m.n_own)) : 0u;
+                                const double2 yy = split_assemble<LPR>(acc, info, m.n_own, xs, xd);
+                                if (info) accumulate_residual(yy.x, yy.y, ss, mx);
+                            }
                         }
                     } else {
                         const float* sv = reinterpret_cast<const float*>(st + L.o_val) - (p0 & ~3);
@@ -1429,7 +1475,8 @@ __global__ void k_gather_b(const long long* __restrict__ perm, const double* __r
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    out[r] = b ? b[perm[r]] : 0.0;
+    const long long i = perm[r];
+    out[r] = (b && i >= 0) ? b[i] : 0.0;
 }
 
 // ||b||_2 with a fixed reduction order (one CTA of 1024 threads).
@@ -1521,7 +1568,9 @@ static const void* persistent_fn_lanes(int lanes)
     case 1: return persistent_fn<1, STAGES, MIXED, 8, 1, SYNC>();
     case 2: return persistent_fn<1, STAGES, MIXED, 8, 2, SYNC>();
     case 4: return persistent_fn<1, STAGES, MIXED, 8, 4, SYNC>();
-    case 8: return persistent_fn<1, STAGES, MIXED, 8, 8, SYNC>();
+    case 8:
+        if constexpr (SYNC == 3) return nullptr;   // split layouts use 1, 2 or 4 lanes
+        else return persistent_fn<1, STAGES, MIXED, 8, 8, SYNC>();
     default: return nullptr;
     }
 }
@@ -1530,9 +1579,20 @@ static const void* persistent_fn_lanes(int lanes)
 // 256 -> 8 (2 CTAs/SM, 96 regs; or 3 stages, 72 regs, 3 CTAs/SM),
 // 480 -> 15 (1 CTA/SM, 128 regs).  lanes = lanes per row (256 threads only);
 // a tile then holds threads / lanes rows.  sync = 0 grid barrier, 1 neighbour
-// flags, 2 asynchronous relaxation (1 and 2: 256 threads, FP64 only).
+// flags, 2 asynchronous relaxation (1 and 2: 256 threads, FP64 only), 3 grid
+// barrier over a split interface layout (256 threads, FP64, lanes 1, 2, 4).
 const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, int sync)
 {
+    if (sync == 3) {
+        // grid barrier with a split interface block: FP64, 256 threads, 1/2/4 lanes
+        if (mixed || threads != 256 || (lanes != 1 && lanes != 2 && lanes != 4)) return nullptr;
+        switch (stages) {
+        case 2: return persistent_fn_lanes<2, false, 3>(lanes);
+        case 3: return persistent_fn_lanes<3, false, 3>(lanes);
+        case 4: return persistent_fn_lanes<4, false, 3>(lanes);
+        default: return nullptr;
+        }
+    }
     if (sync == 1 || sync == 2) {
         if (mixed || threads != 256) return nullptr;
         // every stage count gets its own instantiation: the kernel's stage
@@ -1596,10 +1656,11 @@ cudaError_t launch_scatter_rows(const long long* perm, const double* src, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_b(const long long* perm, const double* b, double* out, int n, JacCtl* ctl, cudaStream_t s)
+cudaError_t launch_gather_b(const long long* perm, const double* b, double* out, int nout, int nb, JacCtl* ctl,
+                            cudaStream_t s)
 {
-    k_gather_b<<<(n + 255) / 256, 256, 0, s>>>(perm, b, out, n);
-    k_bnorm<<<1, 1024, 0, s>>>(b, n, ctl);
+    k_gather_b<<<(nout + 255) / 256, 256, 0, s>>>(perm, b, out, nout);
+    k_bnorm<<<1, 1024, 0, s>>>(b, nb, ctl);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,9 @@ cudaError_t launch_gather_rows(const long long* perm, const double* src, const d
                                int nrhs, cudaStream_t s);
 cudaError_t launch_scatter_rows(const long long* perm, const double* src, const double* d, double* dst, int n,
                                 int nrhs, cudaStream_t s);
-cudaError_t launch_gather_b(const long long* perm, const double* b, double* out, int n, JacCtl* ctl, cudaStream_t s);
+// out[r] = b[perm[r]] (0 where perm[r] < 0), r < nout; ||b||_2 over the nb entries of b.
+cudaError_t launch_gather_b(const long long* perm, const double* b, double* out, int nout, int nb, JacCtl* ctl,
+                            cudaStream_t s);
 cudaError_t launch_arm(JacCtl* ctl, int test, int mixed, int inner, long long k_limit, long long k_delta,
                        double tol, int norm_kind, double* hist, long long hist_cap, long long timeout, int skip,
                        cudaStream_t s);

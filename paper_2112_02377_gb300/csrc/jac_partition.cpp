@@ -6,6 +6,8 @@
 // (Sec. 4.3, block form Eq. (4.4)).
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
 
@@ -254,8 +256,12 @@ double default_row_cost(int64_t off_entries)
 }
 
 void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
-                 int64_t ctas, Tiling& t, const std::vector<double>* row_cost)
+                 int64_t ctas, Tiling& t, const std::vector<double>* row_cost, int64_t align_from, int32_t align)
 {
+    auto aligned_up = [&](int64_t r) -> int64_t {
+        if (align <= 1 || r <= align_from) return r;
+        return std::min<int64_t>(tf.n, align_from + (r - align_from + align - 1) / align * align);
+    };
     t = Tiling();
     t.rows_per_tile = rows_per_tile;
     t.max_entries = max_entries;
@@ -274,6 +280,7 @@ void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, 
         for (int64_t g = 1; g < ctas; ++g) {
             const double target = pre[n] * (double)g / (double)ctas;
             while (cur < n && pre[cur] + 0.5 * (pre[cur + 1] - pre[cur]) < target) ++cur;
+            cur = aligned_up(cur);
             rb[g] = cur;
         }
     }
@@ -297,6 +304,12 @@ void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, 
                 ent += len;
                 ++rows;
                 if (ent > max_entries) break;   // a single oversized row forms its own tile
+            }
+            if (align > 1 && r >= align_from && r + rows < lim && (r + rows - align_from) % align) {
+                // aligned cut: back to the previous boundary, or on to the next one
+                // (the tile then exceeds the staged entries and is read from L2)
+                const int64_t down = (r + rows - align_from) / align * align + align_from;
+                rows = down > r ? down - r : std::min<int64_t>(lim, aligned_up(r + rows)) - r;
             }
             r += rows;
             t.row0.push_back((int32_t)r);
@@ -373,6 +386,199 @@ void make_windows(const ScaledForm& tf, const Tiling& t, int32_t xcap, int32_t m
         }
     }
     w.blk0[nt] = (int32_t)(w.blk.size() / 4);
+}
+
+// ---------------------------------------------------------------- split interface
+
+int32_t split_max_multiplicity(int64_t n, int32_t nsub, const jac_local* sub)
+{
+    if (n < 1 || nsub < 1 || !sub) return 0;
+    std::vector<int32_t> mult(n, 0);
+    int32_t mx = 0;
+    for (int32_t s = 0; s < nsub; ++s) {
+        if (sub[s].n < 0 || (sub[s].n > 0 && !sub[s].l2g)) return 0;
+        for (int32_t l = 0; l < sub[s].n; ++l) {
+            const int64_t g = sub[s].l2g[l];
+            if (g < 0 || g >= n) return 0;
+            mx = std::max(mx, ++mult[g]);
+        }
+    }
+    return mx;
+}
+
+Error make_split_form(int64_t n, int32_t nsub, const jac_local* sub, int32_t warp_rows, SplitForm& out)
+{
+    out = SplitForm();
+    if (n < 1) return Error(JAC_EINVAL, "n must be >= 1");
+    if (n > INT32_MAX - 64) return Error(JAC_EINVAL, "n too large");
+    if (nsub < 1 || nsub > 65536) return Error(JAC_EINVAL, "nsub must be in 1..65536");
+    if (!sub) return Error(JAC_EINVAL, "sub is NULL");
+    if (warp_rows < 1 || warp_rows > 32) return Error(JAC_EINVAL, "bad warp_rows");
+    // ---- validate each local matrix; multiplicities; diagonals
+    std::vector<int32_t> mult(n, 0), stamp(n, -1);
+    std::vector<double> d(n, 0.0);
+    int64_t nnz_all = 0;
+    for (int32_t s = 0; s < nsub; ++s) {
+        const jac_local& L = sub[s];
+        char msg[160];
+        if (L.n < 0 || L.nnz < 0) {
+            std::snprintf(msg, sizeof(msg), "subdomain %d: negative size", s);
+            return Error(JAC_EINVAL, msg);
+        }
+        if (L.n == 0) continue;
+        if (!L.rowptr || !L.l2g || (L.nnz > 0 && (!L.col || !L.val))) {
+            std::snprintf(msg, sizeof(msg), "subdomain %d: NULL array", s);
+            return Error(JAC_EINVAL, msg);
+        }
+        if (L.rowptr[0] != 0 || L.rowptr[L.n] != L.nnz) {
+            std::snprintf(msg, sizeof(msg), "subdomain %d: rowptr must run from 0 to nnz", s);
+            return Error(JAC_EINVAL, msg);
+        }
+        nnz_all += L.nnz;
+        if (nnz_all >= INT32_MAX) return Error(JAC_EINVAL, "total local nnz >= 2^31");
+        for (int32_t l = 0; l < L.n; ++l) {
+            const int64_t g = L.l2g[l];
+            if (g < 0 || g >= n) {
+                std::snprintf(msg, sizeof(msg), "subdomain %d: l2g[%d] = %lld out of range", s, l, (long long)g);
+                return Error(JAC_EINVAL, msg);
+            }
+            if (stamp[g] == s) {
+                std::snprintf(msg, sizeof(msg), "subdomain %d: row %lld listed twice in l2g", s, (long long)g);
+                return Error(JAC_EINVAL, msg);
+            }
+            stamp[g] = s;
+            ++mult[g];
+            if (L.rowptr[l + 1] < L.rowptr[l]) {
+                std::snprintf(msg, sizeof(msg), "subdomain %d: rowptr decreases at %d", s, l);
+                return Error(JAC_EINVAL, msg);
+            }
+            int ndiag = 0;
+            for (int64_t k = L.rowptr[l]; k < L.rowptr[l + 1]; ++k) {
+                if (L.col[k] < 0 || L.col[k] >= L.n) {
+                    std::snprintf(msg, sizeof(msg), "subdomain %d: column index out of range in local row %d", s, l);
+                    return Error(JAC_EINVAL, msg);
+                }
+                if (L.col[k] == l) {
+                    if (++ndiag > 1) {
+                        std::snprintf(msg, sizeof(msg), "subdomain %d: two diagonal entries in local row %d", s, l);
+                        return Error(JAC_EINVAL, msg);
+                    }
+                    d[g] += L.val[k];         // subdomains in ascending order
+                }
+            }
+        }
+    }
+    int32_t max_mult = 0;
+    for (int64_t g = 0; g < n; ++g) {
+        if (mult[g] == 0) {
+            char msg[96];
+            std::snprintf(msg, sizeof(msg), "row %lld belongs to no subdomain", (long long)g);
+            return Error(JAC_EINVAL, msg);
+        }
+        if (d[g] == 0.0 || !std::isfinite(d[g])) {
+            char msg[96];
+            std::snprintf(msg, sizeof(msg), "assembled diagonal of row %lld is %g", (long long)g, d[g]);
+            return Error(JAC_ESINGULAR, msg);
+        }
+        max_mult = std::max(max_mult, mult[g]);
+    }
+    if (max_mult > warp_rows) {
+        char msg[128];
+        std::snprintf(msg, sizeof(msg), "a row is held by %d subdomains; at most %d with %d lanes per row", max_mult,
+                      warp_rows, 32 / warp_rows);
+        return Error(JAC_EINVAL, msg);
+    }
+    // ---- holders of every row, ascending subdomain: (s, local row)
+    std::vector<int64_t> hptr(n + 1, 0);
+    for (int64_t g = 0; g < n; ++g) hptr[g + 1] = hptr[g] + mult[g];
+    std::vector<int32_t> hsub(hptr[n]), hloc(hptr[n]);
+    {
+        std::vector<int64_t> fill(hptr.begin(), hptr.end() - 1);
+        for (int32_t s = 0; s < nsub; ++s)
+            for (int32_t l = 0; l < sub[s].n; ++l) {
+                const int64_t g = sub[s].l2g[l];
+                hsub[fill[g]] = s;
+                hloc[fill[g]++] = l;
+            }
+    }
+    // ---- new order: interiors by subdomain (ascending row), then the interface
+    Plan& P = out.plan;
+    P.splitting = JAC_SUBSTRUCT;
+    P.perm.reserve(n);
+    std::vector<int64_t> cnt(nsub + 1, 0);
+    for (int64_t g = 0; g < n; ++g)
+        if (mult[g] == 1) ++cnt[hsub[hptr[g]] + 1];
+    for (int32_t s = 0; s < nsub; ++s) cnt[s + 1] += cnt[s];
+    const int64_t n_own = cnt[nsub];
+    P.perm.assign(n, -1);
+    {
+        std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+        int64_t f = n_own;
+        for (int64_t g = 0; g < n; ++g) {
+            if (mult[g] == 1) P.perm[fill[hsub[hptr[g]]]++] = g;
+            else P.perm[f++] = g;
+        }
+    }
+    P.iperm.assign(n, 0);
+    for (int64_t r = 0; r < n; ++r) P.iperm[P.perm[r]] = r;
+    out.n = n;
+    out.n_own = n_own;
+    out.n_ifc = n - n_own;
+    out.nnz_local = nnz_all;
+    out.warp_rows = warp_rows;
+    out.max_mult = max_mult;
+    if (out.n_ifc >= (int64_t)1 << 26) return Error(JAC_EINVAL, "interface too large (>= 2^26 rows)");
+    // ---- kernel rows
+    ScaledForm& tf = out.tf;
+    tf.d.resize(n);
+    for (int64_t r = 0; r < n; ++r) tf.d[r] = d[P.perm[r]];
+    tf.rowptr.assign(1, 0);
+    auto push_row = [&](int32_t s, int32_t l) {
+        const jac_local& L = sub[s];
+        for (int64_t k = L.rowptr[l]; k < L.rowptr[l + 1]; ++k) {
+            if (L.col[k] == l) continue;
+            const int64_t gj = L.l2g[L.col[k]];
+            tf.col.push_back((int32_t)P.iperm[gj]);
+            tf.S.push_back(-L.val[k] / d[gj]);
+        }
+        const int64_t len = (int64_t)tf.col.size() - tf.rowptr.back();
+        tf.max_off = std::max(tf.max_off, len);
+        if ((int64_t)tf.col.size() >= INT32_MAX) return false;
+        tf.rowptr.push_back((int32_t)tf.col.size());
+        return true;
+    };
+    out.bmap.reserve(n + (size_t)out.n_ifc * 2);
+    for (int64_t r = 0; r < n_own; ++r) {
+        const int64_t g = P.perm[r];
+        if (!push_row(hsub[hptr[g]], hloc[hptr[g]])) return Error(JAC_EINVAL, "too many entries");
+        out.bmap.push_back(g);
+    }
+    P.part_ptr.assign(cnt.begin(), cnt.end());     // subdomain interiors
+    int64_t pos = 0;                                // slot rows after n_own
+    auto pad_row = [&]() {
+        tf.rowptr.push_back(tf.rowptr.back());
+        out.bmap.push_back(-1);
+        out.slot_info.push_back(0u);
+        ++pos;
+    };
+    for (int64_t i = 0; i < out.n_ifc; ++i) {
+        const int64_t g = P.perm[n_own + i];
+        const int32_t m = mult[g];
+        if (pos % warp_rows + m > warp_rows)
+            while (pos % warp_rows) pad_row();
+        for (int32_t q = 0; q < m; ++q) {
+            if (!push_row(hsub[hptr[g] + q], hloc[hptr[g] + q])) return Error(JAC_EINVAL, "too many entries");
+            out.bmap.push_back(q == 0 ? g : -1);
+            out.slot_info.push_back(q == 0 ? ((uint32_t)i << 6) | (uint32_t)m : 0u);
+            ++pos;
+        }
+        out.partials += m;
+    }
+    tf.n = n_own + pos;
+    if (tf.n > INT32_MAX - 64) return Error(JAC_EINVAL, "too many kernel rows");
+    P.part_ptr.push_back(tf.n);                    // the interface partition
+    P.interface_rows = out.n_ifc;
+    return Error();
 }
 
 }  // namespace jac

@@ -30,7 +30,7 @@ _STATUS_NAMES = ["JAC_OK", "JAC_EINVAL", "JAC_ENOMEM", "JAC_ECUDA", "JAC_ESINGUL
                  "JAC_ETIMEOUT", "JAC_ENUMERIC"]
 
 # Symbols declared in include/jacobi.h (checked by the CPU test suite).
-EXPORTED = ["jac_opts_default", "jac_setup", "jac_setup_batched", "jac_set_x", "jac_set_b", "jac_sweep",
+EXPORTED = ["jac_opts_default", "jac_setup", "jac_setup_batched", "jac_setup_local", "jac_set_x", "jac_set_b", "jac_sweep",
             "jac_solve", "jac_get_x", "jac_get_history", "jac_get_batch_results", "jac_adjoint_grad",
             "jac_stats", "jac_partition_plan", "jac_dependency_lists", "jac_last_error", "jac_free",
             "jac_get_trace", "jac_sweep_noalloc"]
@@ -47,6 +47,11 @@ class jac_csr(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
                 ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("index_base", ctypes.c_int32),
                 ("memory", ctypes.c_int32)]
+
+
+class jac_local(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("l2g", ctypes.c_void_p)]
 
 
 class jac_opts(ctypes.Structure):
@@ -103,6 +108,7 @@ def lib(build_if_needed: bool = True):
                 "jac_opts_default": (None, [P]),
                 "jac_setup": (I32, [P, P, I32, I32, P, P]),
                 "jac_setup_batched": (I32, [I32, P, P, P, P]),
+                "jac_setup_local": (I32, [I64, I32, P, P, P, P]),
                 "jac_set_x": (I32, [P, P, I32]),
                 "jac_set_b": (I32, [P, P, I32]),
                 "jac_sweep": (I32, [P, I32, P]),
@@ -210,6 +216,31 @@ def jac_setup(A, b=None, splitting: int = JAC_BANDROW, nparts: int = 1, o: Optio
     ctx = ctypes.c_void_p()
     st = lib().jac_setup(ctypes.byref(csr), bp, int(splitting), int(nparts), ctypes.byref(o), ctypes.byref(ctx))
     o.node_of_row = None
+    _check(st, None)
+    return ctx
+
+
+def jac_setup_local(n: int, locals_, b=None, o: Optional[jac_opts] = None) -> ctypes.c_void_p:
+    """Substructuring with the interface block split between subdomains:
+    ``locals_[s]`` has n, rowptr, col (local indices), val and l2g (e.g.
+    workloads.LocalCSR), host arrays; b: n doubles (host) or None."""
+    nsub = len(locals_)
+    arr = (jac_local * max(nsub, 1))()
+    keep = []
+    for i, L in enumerate(locals_):
+        rp = np.ascontiguousarray(L.rowptr, dtype=np.int32)
+        cl = np.ascontiguousarray(L.col, dtype=np.int32)
+        vl = np.ascontiguousarray(L.val, dtype=np.float64)
+        lg = np.ascontiguousarray(L.l2g, dtype=np.int32)
+        keep.append((rp, cl, vl, lg))
+        arr[i] = jac_local(n=int(L.n), nnz=int(vl.size), rowptr=rp.ctypes.data, col=cl.ctypes.data,
+                           val=vl.ctypes.data, l2g=lg.ctypes.data)
+    bp, bm, bkeep = _buf(b, np.float64, "b")
+    if b is not None and bm != JAC_MEM_HOST:
+        raise ValueError("b must be host memory")
+    o = o if o is not None else opts()
+    ctx = ctypes.c_void_p()
+    st = lib().jac_setup_local(int(n), int(nsub), arr, bp, ctypes.byref(o), ctypes.byref(ctx))
     _check(st, None)
     return ctx
 

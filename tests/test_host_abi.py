@@ -219,3 +219,81 @@ def test_irregular_workload_shape_and_scipy_copy_keeps_stored_order():
     diag = np.abs(D.diagonal())
     off = np.asarray(abs(D).sum(axis=1)).ravel() - diag
     assert (diag > off).all()
+
+
+# ------------------------------------------------ split interface (jac_setup_local) ----
+
+def _star_locals(nsub):
+    """nsub subdomains, each holding node 0 and one node of its own (node 0
+    is on the interface of all of them)."""
+    locs = []
+    for s in range(nsub):
+        locs.append(W.LocalCSR(2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32),
+                               np.array([4.0, -1.0, -1.0, 4.0]), np.array([0, s + 1], np.int32)))
+    return locs, nsub + 1
+
+
+def _edit(L, **kw):
+    d = dict(n=L.n, rowptr=L.rowptr, col=L.col, val=L.val, l2g=L.l2g)
+    d.update(kw)
+    return W.LocalCSR(**d)
+
+
+@pytest.mark.parametrize("case,status,msg", [
+    ("uncovered", "EINVAL", "belongs to no subdomain"),
+    ("repeated_l2g", "EINVAL", "listed twice"),
+    ("l2g_range", "EINVAL", "out of range"),
+    ("col_range", "EINVAL", "column index out of range"),
+    ("two_diag", "EINVAL", "two diagonal entries"),
+    ("zero_diag", "ESINGULAR", "assembled diagonal"),
+    ("crowded", "EINVAL", "held by 9 subdomains"),
+    ("mixed", "EINVAL", "FP64"),
+    ("async", "EINVAL", "grid sync"),
+])
+def test_split_interface_inputs_are_checked_before_any_device_call(case, status, msg):
+    locs = W.cell_box_locals("laplace7", 4, (2, 1, 1))
+    n, o = 64, J.opts()
+    if case == "uncovered":
+        locs = locs[:1]
+    elif case == "repeated_l2g":
+        g = locs[0].l2g.copy()
+        g[1] = g[0]
+        locs[0] = _edit(locs[0], l2g=g)
+    elif case == "l2g_range":
+        g = locs[1].l2g.copy()
+        g[-1] = 64
+        locs[1] = _edit(locs[1], l2g=g)
+    elif case == "col_range":
+        c = locs[0].col.copy()
+        c[3] = locs[0].n
+        locs[0] = _edit(locs[0], col=c)
+    elif case == "two_diag":
+        L = locs[0]
+        c = L.col.copy()
+        k = int(L.rowptr[5])
+        c[k] = 5 if c[k] != 5 else c[k]
+        c[k + 1] = 5
+        locs[0] = _edit(L, col=c)
+    elif case == "zero_diag":
+        locs = [_edit(L, val=np.where(L.col == np.repeat(np.arange(L.n), np.diff(L.rowptr)), 0.0, L.val))
+                for L in locs]
+    elif case == "crowded":
+        locs, n = _star_locals(9)
+        o = J.opts(lanes_per_row=4)
+    elif case == "mixed":
+        o = J.opts(precision=J.JAC_MIXED)
+    elif case == "async":
+        o = J.opts(sync=J.JAC_SYNC_ASYNC)
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup_local(n, locs, np.ones(n), o)
+    assert ei.value.status == getattr(J, "JAC_" + status) and msg in str(ei.value), str(ei.value)
+
+
+def test_split_interface_setup_without_a_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    locs = W.cell_box_locals("laplace7", 6, (2, 2, 1))
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup_local(216, locs, np.ones(216))
+    assert ei.value.status == J.JAC_ECUDA
