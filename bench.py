@@ -139,11 +139,12 @@ def _traffic_from_profile(kernel_src_hash: str, kernel: str):
         return None
 
 
-def _geometry(st) -> dict:
-    """Kernel instantiation a context runs, from its stats."""
+def _geometry(st, split: bool = False) -> dict:
+    """Kernel instantiation a context runs, from its stats (split: a
+    jac_setup_local context, kernel form 3)."""
     v, rows, cps = st["variant"], st["tile_rows"], st["ctas_per_sm"]
     if v == 2:
-        sync = st["sync"] if st["precision"] == 0 else 0
+        sync = 3 if split else (st["sync"] if st["precision"] == 0 else 0)
         name = (f"k_persistent<1,{st['stages']},{'true' if st['precision'] == 1 else 'false'},"
                 f"{rows // 32},{st['lanes_per_row']},{sync}>")
     elif v == 3:
@@ -216,7 +217,7 @@ def run_reference(args, ws, rank):
     return 0
 
 
-def _solve_line(J, ctx, tol, maxit, A, b, xs, name, prec):
+def _solve_line(J, ctx, tol, maxit, A, b, xs, name, prec, split=False):
     k, rel, st = J.jac_solve(ctx, tol, maxit)
     stt = J.jac_stats(ctx)
     x = J.jac_get_x(ctx)
@@ -225,7 +226,7 @@ def _solve_line(J, ctx, tol, maxit, A, b, xs, name, prec):
             "status": int(st), "relres_reported": rel,
             "relres_true": float(np.linalg.norm(r) / np.linalg.norm(b)), "resinf_true": float(np.max(np.abs(r))),
             "err_vs_xstar": (float(np.linalg.norm(x - xs) / np.linalg.norm(xs)) if xs is not None else None),
-            "us_per_sweep": round(stt["last_ms"] * 1e3 / max(int(k), 1), 2), "kernel": _geometry(stt)["kernel"],
+            "us_per_sweep": round(stt["last_ms"] * 1e3 / max(int(k), 1), 2), "kernel": _geometry(stt, split)["kernel"],
             "n": int(A.n), "nnz": int(A.nnz)}
 
 
@@ -235,8 +236,11 @@ def run_extra(args, local, stream):
     256 batched 7-point systems x 4 right-hand sides to 1e-8, FP64 vs mixed;
     96^3 variable-coefficient diffusion forward + adjoint solve with the
     gradient of L = |x - x_t|^2 / 2 checked by central differences along a
-    random direction of b; and the paper's Q1 FE Laplace replay (33^3 and 65^3
-    nodes, |r|_inf < 1e-8) next to the paper's own iteration counts and times."""
+    random direction of b; the paper's Q1 FE Laplace replay (33^3 and 65^3
+    nodes, |r|_inf < 1e-8) next to the paper's own iteration counts and times,
+    also with the interface block split between 8 and 64 subdomains; and the
+    160^3 system under 4x4x4 substructuring, split interface block against
+    interface rows owned once."""
     from paper_2112_02377_gb300 import jacobi as J
     from paper_2112_02377_gb300 import workloads as W
 
@@ -338,6 +342,52 @@ def run_extra(args, local, stream):
         line["paper_hardware"] = "Xeon E5410 2.33 GHz, one core (Sec. 5.2)"
         J.jac_free(c)
         emit(line)
+        # the same problem with the interface block split between subdomains
+        # (Sec. 4.3 local matrices); the paper's JSS columns at 8 and 64 processes
+        # use its local stopping rule, this library the global test
+        paper_jss = {33: {8: 699, 64: 525}, 65: {8: 2132, 64: 1889}}
+        for sub in ((2, 2, 2), (4, 4, 4)):
+            S = sub[0] * sub[1] * sub[2]
+            locs = W.cell_box_locals("q1", N, sub)
+            o = J.opts(norm=J.JAC_NORM_INF, sweeps_per_graph=64, autotune=1, stream=stream.cuda_stream, device=local)
+            c = J.jac_setup_local(A.n, locs, b, o)
+            line = _solve_line(J, c, 1e-8, 100000, A, b, None, f"paper_q1_{N}cubed_nodes_split_interface", "fp64",
+                               split=True)
+            line["subdomains"] = S
+            line["iterations"] = line["sweeps"] + 1
+            line["paper_iterations_jss_local_test"] = paper_jss[N][S]
+            line["paper_iterations_global"] = paper[N][0]
+            J.jac_free(c)
+            emit(line)
+
+    # ---- split interface block at 160^3, 4x4x4 subdomains: the paper's local
+    # matrices and two-step product against node-based substructuring (the
+    # interface rows owned once); both autotuned, 2000 sweeps each
+    m, sub = 160, (4, 4, 4)
+    A = W.laplace7(m)
+    b = W.solution_and_rhs(A, 0)[1]
+    locs = W.cell_box_locals("laplace7", m, sub)
+    sweeps = 2000
+    base = _algorithmic_bytes(A.n, A.nnz)
+    forms = (("node_based_interface", lambda o: J.jac_setup(A, b, J.JAC_SUBSTRUCT, 0, J.opts(
+                 grid=A.grid, subdomains=sub, autotune=1, sweeps_per_graph=250, stream=stream.cuda_stream,
+                 device=local))),
+             ("split_interface", lambda o: J.jac_setup_local(A.n, locs, b, J.opts(
+                 autotune=1, sweeps_per_graph=250, stream=stream.cuda_stream, device=local))))
+    for name, make in forms:
+        c = make(None)
+        J.jac_sweep(c, 250)
+        J.jac_set_x(c, None)
+        J.jac_sweep(c, sweeps)
+        stt = J.jac_stats(c)
+        us = stt["last_ms"] * 1e3 / sweeps
+        emit({"extra": "substructuring_160cubed_4x4x4", "form": name, "sweeps": sweeps,
+              "us_per_sweep": round(us, 2), "gbs_of_assembled_sweep_bytes": round(base / (us * 1e-6) / 1e9, 1),
+              "bytes_per_sweep_own": stt["bytes_per_sweep_fp64"], "interface_rows": int(stt["interface_rows"]),
+              "interface_partials": int(stt["halo_entries"]) if name == "split_interface" else None,
+              "kernel": _geometry(stt, name == "split_interface")["kernel"], "n": int(A.n),
+              "nnz_stored": int(stt["nnz"])})
+        J.jac_free(c)
     return 0
 
 
@@ -356,6 +406,9 @@ def main():
     ap.add_argument("--profile-variant", type=int, default=0, help="kernel variant of the profiling case (0 = default)")
     ap.add_argument("--profile-rows", type=int, default=0, help="tile rows of the profiling case (0 = default)")
     ap.add_argument("--profile-cps", type=int, default=0, help="CTAs per SM of the profiling case (0 = default)")
+    ap.add_argument("--profile-split", action="store_true",
+                    help="profiling case with the interface block split between 4x4x4 subdomains (local "
+                         "matrices, jac_setup_local) instead of the band-row context")
     ap.add_argument("--extra", action="store_true", help="run the secondary workloads instead (JSON lines)")
     ap.add_argument("--clocks-csv", default="",
                     help="where to keep the nvidia-smi samples of the timed region ({rank} is replaced by the "
@@ -390,7 +443,10 @@ def main():
         o = J.opts(variant=args.profile_variant, sweeps_per_graph=K, device=local,
                    precision=J.JAC_MIXED if mixed else J.JAC_FP64, inner_sweeps=max(2, K),
                    tile_rows=args.profile_rows, ctas_per_sm=args.profile_cps)
-        c = J.jac_setup(A, b, J.JAC_BANDROW, 64, o)
+        if args.profile_split:
+            c = J.jac_setup_local(A.n, W.cell_box_locals("laplace7", GRID, (4, 4, 4)), b, o)
+        else:
+            c = J.jac_setup(A, b, J.JAC_BANDROW, 64, o)
         if mixed:
             J.jac_solve(c, 0.0, 3 * K - 1)        # three launches of K sweeps (cycles of K)
         else:

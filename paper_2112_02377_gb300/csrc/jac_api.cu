@@ -1897,6 +1897,9 @@ jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
     out->last_resinf = h.resinf;
     out->last_ms = c->last_ms;
     out->bytes_per_sweep_fp64 = algorithmic_bytes_fp64(c->n, c->nnz_off);
+    if (c->split)   // kernel rows (rowptr, b, slot metadata) beyond the n iterate rows
+        out->bytes_per_sweep_fp64 += 4.0 * (double)(c->rows - c->n) + 8.0 * (double)(c->rows - c->n) +
+                                     4.0 * (double)(c->rows - c->n_own);
     out->bytes_per_sweep_fp32 = algorithmic_bytes_fp32(c->n, c->nnz_off);
     out->variant = c->variant;
     out->precision = c->precision;
