@@ -217,7 +217,28 @@ def run_reference(args, ws, rank):
     return 0
 
 
-def _solve_line(J, ctx, tol, maxit, A, b, xs, name, prec, split=False):
+def _fp32_bytes(n: int, nnz: int) -> float:
+    # FP32 inner sweep: 8 (nnz - n) [values + columns] + 4(n+1) [row pointers] + 4n [r] + 4n [f in] + 4n [f out]
+    return 8.0 * (nnz - n) + 4.0 * (n + 1) + 12.0 * n
+
+
+def _roofline_fields(bytes_per_sweep: float, us_per_sweep: float) -> dict:
+    peak, kind = _measured_peak()
+    gbs = bytes_per_sweep / (us_per_sweep * 1e-6) / 1e9 if us_per_sweep > 0 else 0.0
+    return {"algorithmic_bytes_per_sweep": bytes_per_sweep, "gbs": round(gbs, 1),
+            "frac_of_measured_hbm": round(gbs / peak, 4), "peak_kind": kind}
+
+
+def _oracle_fields(A, b, budget_s: float = 2.0) -> dict:
+    """The C oracle's sweep on the same matrix, single-threaded, timed on a
+    bounded sample (about budget_s seconds)."""
+    one = cpu_oracle_rate(A, b, 1)
+    k = max(1, min(2000, int(budget_s / max(one, 1e-6))))
+    dt = cpu_oracle_rate(A, b, k)
+    return {"oracle_us_per_sweep": round(dt / k * 1e6, 1), "oracle_sample_sweeps": k, "oracle_cores": 1}
+
+
+def _solve_line(J, ctx, tol, maxit, A, b, xs, name, prec, split=False, inner=128):
     k, rel, st = J.jac_solve(ctx, tol, maxit)
     stt = J.jac_stats(ctx)
     x = J.jac_get_x(ctx)
@@ -227,7 +248,10 @@ def _solve_line(J, ctx, tol, maxit, A, b, xs, name, prec, split=False):
             "relres_true": float(np.linalg.norm(r) / np.linalg.norm(b)), "resinf_true": float(np.max(np.abs(r))),
             "err_vs_xstar": (float(np.linalg.norm(x - xs) / np.linalg.norm(xs)) if xs is not None else None),
             "us_per_sweep": round(stt["last_ms"] * 1e3 / max(int(k), 1), 2), "kernel": _geometry(stt, split)["kernel"],
-            "n": int(A.n), "nnz": int(A.nnz)}
+            "n": int(A.n), "nnz": int(A.nnz),
+            **_roofline_fields(stt["bytes_per_sweep_fp64"] if prec != "mixed" else
+                               (stt["bytes_per_sweep_fp64"] + (inner - 1) * _fp32_bytes(A.n, A.nnz)) / inner,
+                               stt["last_ms"] * 1e3 / max(int(k), 1))}
 
 
 def run_extra(args, local, stream):
@@ -255,7 +279,10 @@ def run_extra(args, local, stream):
                    sync=J.JAC_SYNC_ASYNC if prec == "async" else J.JAC_SYNC_GRID,
                    sweeps_per_graph=256, autotune=1, stream=stream.cuda_stream, device=local)
         c = J.jac_setup(A, b, J.JAC_BANDROW_NNZ, 64, o)
-        emit(_solve_line(J, c, 1e-10, 200000, A, b, xs, "fe27_128cubed_to_1e-10", prec))
+        line = _solve_line(J, c, 1e-10, 200000, A, b, xs, "fe27_128cubed_to_1e-10", prec)
+        if prec == "fp64":
+            line.update(_oracle_fields(A, b))
+        emit(line)
         J.jac_free(c)
     del A, b, xs
 
@@ -275,7 +302,22 @@ def run_extra(args, local, stream):
             rr = b_ - A_.scipy() @ xb
             worst = max(worst, float(np.max(np.linalg.norm(rr, axis=0) / np.linalg.norm(b_, axis=0))))
             off += A_.n
+        swr = sw.reshape(len(mats), 4)
+        if prec == "fp64":
+            mat_b = sum(float(swr[i].max()) * (12.0 * (A_.nnz - A_.n) + 4.0 * (A_.n + 1) + 8.0 * A_.n)
+                        for i, A_ in enumerate(mats))
+            vec_b = sum(float(swr[i].sum()) * 16.0 * A_.n for i, A_ in enumerate(mats))
+        else:
+            mat_b = sum(float(swr[i].max()) * (8.0 * (A_.nnz - A_.n) + 4.0 * (A_.n + 1) + 4.0 * A_.n)
+                        for i, A_ in enumerate(mats))
+            vec_b = sum(float(swr[i].sum()) * 8.0 * A_.n for i, A_ in enumerate(mats))
+        peak, pkind = _measured_peak()
+        gbs_b = (mat_b + vec_b) / (stt["last_ms"] * 1e-3) / 1e9
         emit({"extra": "batched_256x4_to_1e-8", "precision": prec, "seconds": round(stt["last_ms"] / 1e3, 4),
+              "algorithmic_bytes": mat_b + vec_b, "gbs": round(gbs_b, 1),
+              "frac_of_measured_hbm": round(gbs_b / peak, 4), "bytes_note": (
+                  "each system's matrix once per sweep while any of its right-hand sides iterates, "
+                  "vectors per right-hand side sweep (FP32 phases counted at FP32 bytes for mixed)"),
               "sweeps_global": int(k), "status": int(st), "rhs_sweeps_min": int(sw.min()),
               "rhs_sweeps_max": int(sw.max()), "rhs_sweeps_sum": int(sw.sum()), "worst_relres_true": worst,
               "tile_rows": stt["tile_rows"], "ctas_per_sm": stt["ctas_per_sm"], "n": int(stt["n"]),
@@ -340,6 +382,8 @@ def run_extra(args, local, stream):
         line["iterations"] = line["sweeps"] + 1       # Algorithm 1 counts the converged pass
         line["paper_seconds_sequential"] = paper[N][1]
         line["paper_hardware"] = "Xeon E5410 2.33 GHz, one core (Sec. 5.2)"
+        line.update(_oracle_fields(A, b))
+        line["oracle_seconds_full_solve_estimate"] = round(line["oracle_us_per_sweep"] * 1e-6 * line["iterations"], 3)
         J.jac_free(c)
         emit(line)
         # the same problem with the interface block split between subdomains
@@ -381,13 +425,25 @@ def run_extra(args, local, stream):
         J.jac_sweep(c, sweeps)
         stt = J.jac_stats(c)
         us = stt["last_ms"] * 1e3 / sweeps
-        emit({"extra": "substructuring_160cubed_4x4x4", "form": name, "sweeps": sweeps,
+        line = {"extra": "substructuring_160cubed_4x4x4", "form": name, "sweeps": sweeps,
               "us_per_sweep": round(us, 2), "gbs_of_assembled_sweep_bytes": round(base / (us * 1e-6) / 1e9, 1),
               "bytes_per_sweep_own": stt["bytes_per_sweep_fp64"], "interface_rows": int(stt["interface_rows"]),
               "interface_partials": int(stt["halo_entries"]) if name == "split_interface" else None,
               "kernel": _geometry(stt, name == "split_interface")["kernel"], "n": int(A.n),
-              "nnz_stored": int(stt["nnz"])})
+              "nnz_stored": int(stt["nnz"]), **_roofline_fields(stt["bytes_per_sweep_fp64"], us)}
         J.jac_free(c)
+        if name == "split_interface":
+            from oracle import oracle as O
+            P = O.split_prepare(locs, A.n)
+            x = np.zeros(A.n)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                x = O.split_sweep(P, b, x)[0]
+            line.update({"oracle_us_per_sweep": round((time.perf_counter() - t0) / 3 * 1e6, 1),
+                         "oracle_sample_sweeps": 3, "oracle_cores": 1})
+        else:
+            line.update(_oracle_fields(A, b, budget_s=1.0))
+        emit(line)
     return 0
 
 
