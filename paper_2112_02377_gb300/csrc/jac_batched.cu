@@ -22,7 +22,10 @@
 
 namespace jac {
 
-constexpr int BCHUNK = 3;    // entries per row whose NRHS-wide x gathers are issued together
+// Entries per row whose NRHS-wide x gathers are issued together.  Measured
+// on GB300 with 4 right-hand sides: larger chunks spill at the kernel's 128
+// registers and lose more than the extra gathers in flight gain.
+constexpr int BCHUNK = 3;
 
 __device__ __forceinline__ void b_consumer_sync(int nthreads)
 {
@@ -258,8 +261,13 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
         double* xd = v.x[xb ^ 1];
         const float* es = v.e[pos & 1];
         float* ed = v.e[(pos + 1) & 1];
-        double ss[NRHS];
-        unsigned long long mx[NRHS];
+        // One tile loop per phase type (FP64 sweeps with the norms, FP32 inner
+        // sweeps without): the FP32 loop then carries no norm accumulators.
+        auto run_tiles = [&](auto tag) {
+        using Real = decltype(tag);
+        constexpr bool F64 = sizeof(Real) == 8;
+        double ss[F64 ? NRHS : 1];
+        unsigned long long mx[F64 ? NRHS : 1];
         int cur = -1, msk = ALL;
         int pidx = -1;   // the CTA's partial slot of the current system: systems met so far - 1
         // per-(CTA, system) partials: block reduction, then the last CTA of the system decides
@@ -340,12 +348,16 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
             const int ti = tb + i;
             const int sys = __ldg(bt.tile_sys + ti);
             if (sys != cur) {
-                if (cur >= 0 && msk != ALL && norm_ph) finish(cur);
+                if constexpr (F64) {
+                    if (cur >= 0 && msk != ALL) finish(cur);
+                }
                 cur = sys;
                 ++pidx;
                 msk = ld_volatile_i32(bt.mask + sys);
+                if constexpr (F64) {
 #pragma unroll
-                for (int q = 0; q < NRHS; ++q) { ss[q] = 0.0; mx[q] = 0; }
+                    for (int q = 0; q < NRHS; ++q) { ss[q] = 0.0; mx[q] = 0; }
+                }
             }
             const int sidx = (int)(jc % STAGES);
             uint64_t* bar = &full[sidx];
@@ -368,7 +380,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
                 const int r = r0 + tid;
                 const bool in = r < r1;
                 const int kb = in ? srp[r] : 0, len = in ? srp[r + 1] - kb : 0;
-                if (norm_ph) {
+                if constexpr (F64) {
                     const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
                     const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (size_t)(r0 & ~1) * NRHS;
                     double acc[NRHS], xi[NRHS];
@@ -421,7 +433,12 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
             __syncwarp();
             if (lane == 0) mbar_arrive_b(&empty[sidx]);
         }
-        if (cur >= 0 && msk != ALL && norm_ph) finish(cur);
+        if constexpr (F64) {
+            if (cur >= 0 && msk != ALL) finish(cur);
+        }
+        };
+        if (norm_ph) run_tiles(double(0));
+        else run_tiles(float(0));
         // ---- grid barrier
         b_consumer_sync(CT);
         if (tid == 0) {

@@ -172,3 +172,75 @@ def test_full_size_160_cube_split_sweep_against_oracle_and_substructuring():
     finally:
         J.jac_free(ctx)
         J.jac_free(ref)
+
+
+def _random_unstructured_locals(n, nsub, seed):
+    """Overlapping random node sets (rows held by 1 to 5 subdomains), random
+    local patterns stored in random order, off-diagonal pieces of both signs,
+    local diagonals sharing a dominance margin; plus an empty subdomain and
+    one made only of rows that other subdomains also hold."""
+    rng = np.random.default_rng(seed)
+    owner = rng.integers(0, nsub, n)
+    sets = [list(np.flatnonzero(owner == s)) for s in range(nsub)]
+    for g in rng.choice(n, n // 5, replace=False):         # extra holders
+        for s in rng.choice(nsub, rng.integers(1, 5), replace=False):
+            if g not in sets[s]:
+                sets[s].append(g)
+    shared = [g for g in range(n) if sum(g in S for S in sets) >= 2][:40]
+    sets.append(shared)                                    # only interface rows
+    sets.append([])                                        # empty
+    locs = []
+    for S in sets:
+        nodes = np.array(sorted(S), dtype=np.int32)
+        nl = nodes.size
+        rowptr, col, val = [0], [], []
+        for l in range(nl):
+            k = int(rng.integers(0, min(nl, 30))) if nl > 1 else 0
+            others = rng.choice([j for j in range(nl) if j != l], k, replace=False) if k else []
+            ent = [(int(j), float(rng.uniform(-1, 1))) for j in others] + [(l, 0.0)]
+            rng.shuffle(ent)
+            for j, v in ent:
+                col.append(j)
+                val.append(v)
+            rowptr.append(len(col))
+        locs.append(W.LocalCSR(nl, np.array(rowptr, np.int32), np.array(col, np.int32), np.array(val), nodes))
+    absoff = np.zeros(n)
+    for L in locs:
+        rows = np.repeat(np.arange(L.n), np.diff(L.rowptr))
+        np.add.at(absoff, L.l2g[rows], np.where(L.col != rows, np.abs(L.val), 0.0))
+    for L in locs:
+        rows = np.repeat(np.arange(L.n), np.diff(L.rowptr))
+        dg = L.col == rows
+        L.val[dg] = (1.2 * absoff[L.l2g[rows[dg]]] + 0.5) * rng.uniform(0.3, 1.0, dg.sum())
+    return locs
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_unstructured_local_matrices_with_mixed_sign_pieces(lanes):
+    n = 6000
+    locs = _random_unstructured_locals(n, 9, 5)
+    P = O.split_prepare(locs, n)
+    assert P.mult.max() >= 4 and locs[-1].n == 0
+    rng = np.random.default_rng(3)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    y1, ss1, _ = O.split_sweep(P, b, x0)
+    # scale of a row: |b| + sum over subdomains of |local off-diagonal terms|, over |d|
+    sc = np.abs(b).copy()
+    for L in locs:
+        rows = np.repeat(np.arange(L.n), np.diff(L.rowptr))
+        off = L.col != rows
+        np.add.at(sc, L.l2g[rows[off]], np.abs(L.val[off] * x0[L.l2g[L.col[off]]]))
+    sc /= np.abs(P.d)
+    ctx = J.jac_setup_local(n, locs, b, J.opts(lanes_per_row=lanes, debug=1))
+    try:
+        J.jac_set_x(ctx, x0)
+        rel = J.jac_sweep(ctx, 1)
+        err = np.abs(J.jac_get_x(ctx) - y1)
+        assert np.all(err <= RTOL * sc), f"worst {np.max(err / sc):.3e}"
+        assert abs(rel - np.sqrt(ss1) / np.linalg.norm(b)) <= 1e-12 * np.sqrt(ss1) / np.linalg.norm(b) + 1e-15
+        k, r, st = J.jac_solve(ctx, 1e-10, 5000)
+        xs, ko, ro, _ = O.split_solve(P, b, None, tol=1e-10, maxit=5000)
+        assert st == J.JAC_OK and abs(k - ko) <= 1
+        assert np.max(np.abs(J.jac_get_x(ctx) - xs)) <= 1e-9 * np.max(np.abs(xs))
+    finally:
+        J.jac_free(ctx)
