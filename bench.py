@@ -222,11 +222,31 @@ def _fp32_bytes(n: int, nnz: int) -> float:
     return 8.0 * (nnz - n) + 4.0 * (n + 1) + 12.0 * n
 
 
-def _roofline_fields(bytes_per_sweep: float, us_per_sweep: float) -> dict:
+# GB300's FP64 pipe: 2 lane-operations per SM per clock (152 SMs, 2070 MHz
+# maximum SM clock), about 629 G FP64 instructions per second.
+FP64_PIPE_PER_S = 2.0 * 152 * 2.070e9
+
+
+def _fp64_instr(n: int, nnz: int, nrhs: int = 1) -> float:
+    # algorithmic FP64 instructions of one FP64 sweep: per row and right-hand
+    # side one DFMA per off-diagonal entry, r = y' - y and the r*r accumulation
+    return float(nrhs) * ((nnz - n) + 2.0 * n)
+
+
+def _roofline_fields(bytes_per_sweep: float, us_per_sweep: float, fp64_instr_per_sweep: float = 0.0) -> dict:
+    """Both floors of a sweep: algorithmic bytes at the measured copy bandwidth
+    and algorithmic FP64 instructions at the FP64 pipe's peak; the larger one
+    binds, and frac is that floor over the measured time."""
     peak, kind = _measured_peak()
     gbs = bytes_per_sweep / (us_per_sweep * 1e-6) / 1e9 if us_per_sweep > 0 else 0.0
+    t_hbm = bytes_per_sweep / (peak * 1e9) * 1e6
+    t_fp64 = fp64_instr_per_sweep / FP64_PIPE_PER_S * 1e6
+    bound = "fp64" if t_fp64 > t_hbm else "hbm"
     return {"algorithmic_bytes_per_sweep": bytes_per_sweep, "gbs": round(gbs, 1),
-            "frac_of_measured_hbm": round(gbs / peak, 4), "peak_kind": kind}
+            "frac_of_measured_hbm": round(gbs / peak, 4), "peak_kind": kind,
+            "fp64_instr_per_sweep": fp64_instr_per_sweep,
+            "frac_of_fp64_pipe": round(t_fp64 / us_per_sweep, 4) if us_per_sweep > 0 else None,
+            "bound": bound, "frac_of_bound": round(max(t_hbm, t_fp64) / us_per_sweep, 4) if us_per_sweep > 0 else None}
 
 
 def _oracle_fields(A, b, budget_s: float = 2.0) -> dict:
@@ -251,7 +271,8 @@ def _solve_line(J, ctx, tol, maxit, A, b, xs, name, prec, split=False, inner=128
             "n": int(A.n), "nnz": int(A.nnz),
             **_roofline_fields(stt["bytes_per_sweep_fp64"] if prec != "mixed" else
                                (stt["bytes_per_sweep_fp64"] + (inner - 1) * _fp32_bytes(A.n, A.nnz)) / inner,
-                               stt["last_ms"] * 1e3 / max(int(k), 1))}
+                               stt["last_ms"] * 1e3 / max(int(k), 1),
+                               _fp64_instr(A.n, A.nnz) if prec != "mixed" else _fp64_instr(A.n, A.nnz) / inner)}
 
 
 def run_extra(args, local, stream):
@@ -313,9 +334,19 @@ def run_extra(args, local, stream):
             vec_b = sum(float(swr[i].sum()) * 8.0 * A_.n for i, A_ in enumerate(mats))
         peak, pkind = _measured_peak()
         gbs_b = (mat_b + vec_b) / (stt["last_ms"] * 1e-3) / 1e9
+        # FP64 instructions: every (system, right-hand side) FP64 sweep (all of them
+        # in FP64; one in inner_sweeps for mixed)
+        f64 = sum(float(swr[i].sum()) * ((A_.nnz - A_.n) / A_.n + 2.0) * A_.n for i, A_ in enumerate(mats))
+        if prec == "mixed":
+            f64 /= 128.0
+        t_hbm = (mat_b + vec_b) / (peak * 1e9)
+        t_f64 = f64 / FP64_PIPE_PER_S
         emit({"extra": "batched_256x4_to_1e-8", "precision": prec, "seconds": round(stt["last_ms"] / 1e3, 4),
               "algorithmic_bytes": mat_b + vec_b, "gbs": round(gbs_b, 1),
-              "frac_of_measured_hbm": round(gbs_b / peak, 4), "bytes_note": (
+              "frac_of_measured_hbm": round(gbs_b / peak, 4), "fp64_instr": f64,
+              "frac_of_fp64_pipe": round(t_f64 / (stt["last_ms"] * 1e-3), 4),
+              "bound": "fp64" if t_f64 > t_hbm else "hbm",
+              "frac_of_bound": round(max(t_f64, t_hbm) / (stt["last_ms"] * 1e-3), 4), "bytes_note": (
                   "each system's matrix once per sweep while any of its right-hand sides iterates, "
                   "vectors per right-hand side sweep (FP32 phases counted at FP32 bytes for mixed)"),
               "sweeps_global": int(k), "status": int(st), "rhs_sweeps_min": int(sw.min()),
@@ -430,7 +461,10 @@ def run_extra(args, local, stream):
               "bytes_per_sweep_own": stt["bytes_per_sweep_fp64"], "interface_rows": int(stt["interface_rows"]),
               "interface_partials": int(stt["halo_entries"]) if name == "split_interface" else None,
               "kernel": _geometry(stt, name == "split_interface")["kernel"], "n": int(A.n),
-              "nnz_stored": int(stt["nnz"]), **_roofline_fields(stt["bytes_per_sweep_fp64"], us)}
+              "nnz_stored": int(stt["nnz"]),
+              **_roofline_fields(stt["bytes_per_sweep_fp64"], us,
+                                 _fp64_instr(A.n, A.nnz) + (float(stt["halo_entries"]) if name == "split_interface"
+                                                            else 0.0))}
         J.jac_free(c)
         if name == "split_interface":
             from oracle import oracle as O

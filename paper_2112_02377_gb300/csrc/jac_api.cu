@@ -91,6 +91,7 @@ struct jac_ctx {
     int lanes = 1;                        // lanes per row (persistent variant, 256 threads)
     const void* pfn64 = nullptr;
     const void* pfnmix = nullptr;
+    const void* pfnmix32 = nullptr;    // batched mixed: the FP32 sweeps of a cycle (pfnmix: its FP64 pass)
     int K = 64;
     cudaGraphExec_t g64 = nullptr, gmix = nullptr, gcert = nullptr;
     bool no_graph = false;
@@ -286,14 +287,33 @@ DevBatch devbatch(const jac_ctx* c)
     return b;
 }
 
+// Refinement cycles of a batched mixed graph step: K sweeps rounded up to
+// whole cycles of inner_sweeps.
+int batched_cycles_per_step(const jac_ctx* c)
+{
+    const int m = std::max(2, c->o.inner_sweeps);
+    return std::max(1, (c->K + m - 1) / m);
+}
+
 // Enqueue one "graph step": K sweeps (FP64) or one refinement cycle block (mixed).
 jac_status enqueue_step(jac_ctx* c, bool mixed)
 {
     cudaStream_t s = stream_of(c);
     if (c->batched) {
-        CK(c, launch_reset_bar(c->d_ctl, s));
-        CK(c, launch_batched(mixed ? c->pfnmix : c->pfn64, c->grid, c->threads, c->smem, devmat(c), devvec(c),
-                             devtiles(c), devbatch(c), c->d_ctl, c->K, s));
+        if (!mixed) {
+            CK(c, launch_reset_bar(c->d_ctl, s));
+            CK(c, launch_batched(c->pfn64, c->grid, c->threads, c->smem, devmat(c), devvec(c), devtiles(c),
+                                 devbatch(c), c->d_ctl, c->K, s));
+            return JAC_OK;
+        }
+        // whole refinement cycles: the FP64 pass, then the FP32 sweeps, each a
+        // launch of its own (a launch after a converged pass returns at once)
+        for (int cyc = 0; cyc < batched_cycles_per_step(c); ++cyc)
+            for (const void* fn : {c->pfnmix, c->pfnmix32}) {
+                CK(c, launch_reset_bar(c->d_ctl, s));
+                CK(c, launch_batched(fn, c->grid, c->threads, c->smem, devmat(c), devvec(c), devtiles(c),
+                                     devbatch(c), c->d_ctl, c->o.inner_sweeps, s));
+            }
         return JAC_OK;
     }
     if (c->variant >= 2) {
@@ -1445,18 +1465,21 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
         const int64_t budget = 27 * 1024 - (int64_t)rows * (4 + 8 * nrhs) - 1024;
         c->emax = (int)std::min<int64_t>(cap_entries, std::max<int64_t>(rows, budget / 12));
     }
-    c->pfn64 = batched_kernel(nrhs, false, rows);
-    c->pfnmix = batched_kernel(nrhs, true, rows);
+    c->pfn64 = batched_kernel(nrhs, false, rows, 0);
+    c->pfnmix = batched_kernel(nrhs, true, rows, 1);
+    c->pfnmix32 = batched_kernel(nrhs, true, rows, 2);
     c->smem = batched_smem_bytes(rows, c->emax, nrhs, c->stages);
     c->threads = batched_threads(rows);
     int per_sm = 0;
     {
         CK(nullptr, cudaFuncSetAttribute(c->pfn64, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
         CK(nullptr, cudaFuncSetAttribute(c->pfnmix, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
-        int a1 = 0, a2 = 0;
+        CK(nullptr, cudaFuncSetAttribute(c->pfnmix32, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem));
+        int a1 = 0, a2 = 0, a3 = 0;
         CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a1, c->pfn64, c->threads, c->smem));
         CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, c->pfnmix, c->threads, c->smem));
-        per_sm = std::min(std::min(a1, a2), rows == 96 ? 4 : 2);
+        CK(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a3, c->pfnmix32, c->threads, c->smem));
+        per_sm = std::min(std::min(std::min(a1, a2), a3), rows == 96 ? 4 : 2);
     }
     if (per_sm < 1) return fail(nullptr, JAC_EINVAL, "batched kernel cannot be made co-resident");
     c->grid = per_sm * prop.multiProcessorCount;
@@ -1691,7 +1714,9 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
     int stalled = 0;
     // Every step runs K sweeps unless the solve is over, so a finished solve
     // needs at most (maxit + inner + 1) / K + 2 steps; more means a defect.
-    const long long per_step = (c->variant == 1 && mixed) ? c->o.inner_sweeps : c->K;
+    const long long per_step = (c->variant == 1 && mixed) ? c->o.inner_sweeps
+                               : (c->batched && mixed) ? (long long)batched_cycles_per_step(c) * std::max(2, c->o.inner_sweeps)
+                                                       : c->K;
     const long long step_cap = (maxit + (long long)c->o.inner_sweeps + 1) / per_step + 4;
     long long steps = 1;
     for (;;) {

@@ -22,10 +22,12 @@
 
 namespace jac {
 
-// Entries per row whose NRHS-wide x gathers are issued together.  Measured
-// on GB300 with 4 right-hand sides: larger chunks spill at the kernel's 128
-// registers and lose more than the extra gathers in flight gain.
-constexpr int BCHUNK = 3;
+// Entries per row whose NRHS-wide x gathers are issued together: 3 in the
+// FP64 sweeps (bound by the FP64 pipe; more would spill at 128 registers),
+// 6 in the FP32 inner sweeps, which are bound by L2 gather latency and run in
+// a kernel of their own (a 7-point row's gathers in one round trip).
+template <class Real>
+constexpr int bchunk() { return sizeof(Real) == 4 ? 6 : 3; }
 
 __device__ __forceinline__ void b_consumer_sync(int nthreads)
 {
@@ -94,6 +96,7 @@ template <int NRHS, class Real, class LdT, class LdC>
 __device__ __forceinline__ void brow_dot(Real (&acc)[NRHS], int kb, int len, const Real* __restrict__ xs, LdT ldt,
                                          LdC ldc)
 {
+    constexpr int BCHUNK = bchunk<Real>();
     int lmax = (int)__reduce_max_sync(__activemask(), (unsigned)len);
     for (int o = 0; o < lmax; o += BCHUNK) {
         Real xv[BCHUNK][NRHS];
@@ -115,9 +118,14 @@ __device__ __forceinline__ void brow_dot(Real (&acc)[NRHS], int kb, int len, con
     }
 }
 
-template <int NRHS, int STAGES, bool MIXED, int NWM>
+// PART: 0 = every phase of the launch's sweeps; for the mixed cycle, 1 = its
+// FP64 residual pass only, 2 = its FP32 inner sweeps only.  A mixed graph step
+// alternates a PART 1 and a PART 2 launch per cycle, so the FP32 sweeps run in
+// a kernel without the FP64 code and its registers.
+template <int NRHS, int STAGES, bool MIXED, int NWM, int PART = 0>
 __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBatch bt, JacCtl* ctl, int max_sweeps)
 {
+    static_assert(PART == 0 || MIXED, "the split cycle is for mixed solves");
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int CT = NWM * 32, NW = NWM, ROWS = CT;
     const BStageLayout L = bstage_layout(ROWS, t.emax, NRHS);
@@ -167,6 +175,12 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
     if (!MIXED && !s_test) {
         const long long rem = s_klim - s_k;
         ksw = (int)(rem < (long long)ksw ? (rem > 0 ? rem : 0) : ksw);
+    }
+    // a split-cycle launch runs exactly its phases from the cycle position
+    if constexpr (PART == 1) ksw = (s_phase == 0) ? (ksw < 1 ? ksw : 1) : 0;
+    if constexpr (PART == 2) {
+        const int left = s_phase >= 1 ? s_inner - s_phase : 0;
+        ksw = ksw < left ? ksw : left;
     }
     const long long njobs = (long long)ksw * nt;
     const int inner = s_inner, phase0 = s_phase, emax = t.emax;
@@ -437,7 +451,9 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
             if (cur >= 0 && msk != ALL) finish(cur);
         }
         };
-        if (norm_ph) run_tiles(double(0));
+        if constexpr (PART == 1) run_tiles(double(0));
+        else if constexpr (PART == 2) run_tiles(float(0));
+        else if (norm_ph) run_tiles(double(0));
         else run_tiles(float(0));
         // ---- grid barrier
         b_consumer_sync(CT);
@@ -483,30 +499,42 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
     }
 }
 
-template <int NRHS, bool MIXED, int NWM>
+template <int NRHS, bool MIXED, int NWM, int PART = 0>
 static const void* batched_fn()
 {
-    return reinterpret_cast<const void*>(&k_batched<NRHS, 4, MIXED, NWM>);
+    return reinterpret_cast<const void*>(&k_batched<NRHS, 4, MIXED, NWM, PART>);
+}
+
+template <int NRHS, int NWM>
+static const void* batched_fn_part(bool mixed, int part)
+{
+    if (!mixed) return part == 0 ? batched_fn<NRHS, false, NWM>() : nullptr;
+    switch (part) {
+    case 1: return batched_fn<NRHS, true, NWM, 1>();
+    case 2: return batched_fn<NRHS, true, NWM, 2>();
+    default: return nullptr;
+    }
 }
 
 // Geometries: 224-row tiles (7 math warps + producer, 2 CTAs/SM) or 96-row
 // tiles (3 + 1 warps, 4 CTAs/SM: finer tiles for small systems).  Both leave
-// 128 registers a thread (16 warps per SM).
-const void* batched_kernel(int nrhs, bool mixed, int rows)
+// 128 registers a thread (16 warps per SM).  part: 0 = FP64 solves; 1 / 2 =
+// the FP64 pass / the FP32 sweeps of a mixed refinement cycle.
+const void* batched_kernel(int nrhs, bool mixed, int rows, int part)
 {
     if (rows == 224) {
         switch (nrhs) {
-        case 1: return mixed ? batched_fn<1, true, 7>() : batched_fn<1, false, 7>();
-        case 2: return mixed ? batched_fn<2, true, 7>() : batched_fn<2, false, 7>();
-        case 4: return mixed ? batched_fn<4, true, 7>() : batched_fn<4, false, 7>();
+        case 1: return batched_fn_part<1, 7>(mixed, part);
+        case 2: return batched_fn_part<2, 7>(mixed, part);
+        case 4: return batched_fn_part<4, 7>(mixed, part);
         default: return nullptr;
         }
     }
     if (rows == 96) {
         switch (nrhs) {
-        case 1: return mixed ? batched_fn<1, true, 3>() : batched_fn<1, false, 3>();
-        case 2: return mixed ? batched_fn<2, true, 3>() : batched_fn<2, false, 3>();
-        case 4: return mixed ? batched_fn<4, true, 3>() : batched_fn<4, false, 3>();
+        case 1: return batched_fn_part<1, 3>(mixed, part);
+        case 2: return batched_fn_part<2, 3>(mixed, part);
+        case 4: return batched_fn_part<4, 3>(mixed, part);
         default: return nullptr;
         }
     }

@@ -32,7 +32,8 @@ cudaError_t launch_arm(JacCtl* ctl, int test, int mixed, int inner, long long k_
                        cudaStream_t s);
 cudaError_t launch_reset_iterate(JacCtl* ctl, cudaStream_t s);
 cudaError_t launch_reset_bar(JacCtl* ctl, cudaStream_t s);
-const void* batched_kernel(int nrhs, bool mixed, int rows);
+// part: 0 = FP64 solves; 1 / 2 = the FP64 pass / the FP32 sweeps of a mixed cycle
+const void* batched_kernel(int nrhs, bool mixed, int rows, int part);
 int batched_smem_bytes(int rows, int emax, int nrhs, int stages);
 int batched_threads(int rows);
 cudaError_t launch_batched(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
