@@ -147,6 +147,8 @@ def _geometry(st, split: bool = False) -> dict:
         sync = 3 if split else (st["sync"] if st["precision"] == 0 else 0)
         name = (f"k_persistent<1,{st['stages']},{'true' if st['precision'] == 1 else 'false'},"
                 f"{rows // 32},{st['lanes_per_row']},{sync}>")
+        if st["precision"] == 1:   # a mixed cycle: FP32 sweeps (part 2) after the FP64 pass (part 1)
+            name = name[:-1] + ",2> + ,1>"
     elif v == 3:
         name = "k_halo<3,false>"
     else:

@@ -287,9 +287,9 @@ DevBatch devbatch(const jac_ctx* c)
     return b;
 }
 
-// Refinement cycles of a batched mixed graph step: K sweeps rounded up to
-// whole cycles of inner_sweeps.
-int batched_cycles_per_step(const jac_ctx* c)
+// Refinement cycles of a mixed graph step of the persistent kernels: K sweeps
+// rounded up to whole cycles of inner_sweeps.
+int mixed_cycles_per_step(const jac_ctx* c)
 {
     const int m = std::max(2, c->o.inner_sweeps);
     return std::max(1, (c->K + m - 1) / m);
@@ -308,7 +308,7 @@ jac_status enqueue_step(jac_ctx* c, bool mixed)
         }
         // whole refinement cycles: the FP64 pass, then the FP32 sweeps, each a
         // launch of its own (a launch after a converged pass returns at once)
-        for (int cyc = 0; cyc < batched_cycles_per_step(c); ++cyc)
+        for (int cyc = 0; cyc < mixed_cycles_per_step(c); ++cyc)
             for (const void* fn : {c->pfnmix, c->pfnmix32}) {
                 CK(c, launch_reset_bar(c->d_ctl, s));
                 CK(c, launch_batched(fn, c->grid, c->threads, c->smem, devmat(c), devvec(c), devtiles(c),
@@ -319,6 +319,18 @@ jac_status enqueue_step(jac_ctx* c, bool mixed)
     if (c->variant >= 2) {
         CK(c, launch_reset_bar(c->d_ctl, s));
         if (c->ns && !mixed) CK(c, cudaMemsetAsync(c->d_done, 0, sizeof(unsigned) * DONE_STRIDE * c->grid, s));
+        if (mixed && c->pfnmix32) {
+            // whole refinement cycles, two launches each (see the batched case)
+            bool first = true;   // the barrier counter was reset above for the first launch
+            for (int cyc = 0; cyc < mixed_cycles_per_step(c); ++cyc)
+                for (const void* fn : {c->pfnmix, c->pfnmix32}) {
+                    if (!first) CK(c, launch_reset_bar(c->d_ctl, s));
+                    first = false;
+                    CK(c, launch_persistent(fn, c->grid, c->threads, c->smem, devmat(c), devvec(c), devtiles(c),
+                                            c->d_ctl, c->o.inner_sweeps, s));
+                }
+            return JAC_OK;
+        }
         const void* fn = mixed ? c->pfnmix : (c->certify ? c->pfn64grid : c->pfn64);
         CK(c, launch_persistent(fn, c->grid, c->threads, c->smem, devmat(c), devvec(c), devtiles(c), c->d_ctl, c->K,
                                 s));
@@ -864,8 +876,10 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
             const int form = sp ? 3 : c->sync;
             c->pfn64 = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, form);
             c->pfn64grid = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, sp ? 3 : JAC_SYNC_GRID);
-            // split layouts are FP64 only: no mixed kernel
-            c->pfnmix = sp ? nullptr : persistent_kernel(c->rows_per_tile, c->stages, true, c->lanes, false);
+            // split layouts are FP64 only: no mixed kernels.  A mixed cycle runs as
+            // two launches: the FP64 residual pass, then the FP32 inner sweeps.
+            c->pfnmix = sp ? nullptr : persistent_kernel(c->rows_per_tile, c->stages, true, c->lanes, 0, 1);
+            c->pfnmix32 = sp ? nullptr : persistent_kernel(c->rows_per_tile, c->stages, true, c->lanes, 0, 2);
             c->smem = persistent_smem_bytes(rows, c->emax, c->stages);
         }
         c->threads = (c->variant == 3) ? 256 + 32 : persistent_threads(c->rows_per_tile);
@@ -873,6 +887,16 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         auto occupancy = [&](int smem_bytes) -> int {
             if (!c->pfn64 || (!c->pfnmix && !sp)) return 0;
+            if (c->pfnmix32 && c->variant == 2) {
+                int a4 = 0;
+                if (cudaFuncSetAttribute(c->pfnmix32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
+                        cudaSuccess ||
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a4, c->pfnmix32, c->threads, smem_bytes) !=
+                        cudaSuccess || a4 < 1) {
+                    cudaGetLastError();
+                    return 0;
+                }
+            }
             const void* fmix = c->pfnmix ? c->pfnmix : c->pfn64;
             if (cudaFuncSetAttribute(c->pfn64, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess ||
                 cudaFuncSetAttribute(fmix, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess) {
@@ -1715,7 +1739,8 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
     // Every step runs K sweeps unless the solve is over, so a finished solve
     // needs at most (maxit + inner + 1) / K + 2 steps; more means a defect.
     const long long per_step = (c->variant == 1 && mixed) ? c->o.inner_sweeps
-                               : (c->batched && mixed) ? (long long)batched_cycles_per_step(c) * std::max(2, c->o.inner_sweeps)
+                               : (mixed && (c->batched || c->pfnmix32))
+                                   ? (long long)mixed_cycles_per_step(c) * std::max(2, c->o.inner_sweeps)
                                                        : c->K;
     const long long step_cap = (maxit + (long long)c->o.inner_sweeps + 1) / per_step + 4;
     long long steps = 1;

@@ -375,10 +375,15 @@ __device__ __forceinline__ void consumer_sync()
 // CTA publishes its latest residual sums; CTA 0 adds them into an estimate
 // of the test value and stops the launch when it passes.  The estimate mixes
 // passes, so jac_solve certifies the result with a synchronous evaluation.
-template <int RPT, int STAGES, bool MIXED, int NWM, int LPR, int SYNC>
+//
+// PART splits a mixed refinement cycle into two launches: 1 = its FP64
+// residual pass, 2 = its FP32 inner sweeps (0 = every phase).  Each part then
+// holds only its own phase's code and registers.
+template <int RPT, int STAGES, bool MIXED, int NWM, int LPR, int SYNC, int PART = 0>
 __global__ void __maxnreg__(NWM == 8 ? (STAGES == 3 ? 72 : 96) : 128)   // STAGES 3 with 8 math warps: 3 CTAs/SM
 k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
 {
+    static_assert(PART == 0 || (MIXED && SYNC == 0), "only the mixed cycle is split");
     constexpr bool NS = (SYNC == 1);      // neighbour-synchronised sweeps
     constexpr bool ASYNC = (SYNC == 2);   // asynchronous (chaotic) relaxation
     constexpr bool SPLIT = (SYNC == 3);   // grid barrier; rows from n_own on are slot rows of a split interface
@@ -445,6 +450,12 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         const long long rem = s_klim - s_k;
         ksw = (int)(rem < (long long)ksw ? (rem > 0 ? rem : 0) : ksw);
     }
+    // a split-cycle launch runs exactly its phases from the cycle position
+    if constexpr (PART == 1) ksw = (s_phase == 0) ? (ksw < 1 ? ksw : 1) : 0;
+    if constexpr (PART == 2) {
+        const int left = s_phase >= 1 ? s_inner - s_phase : 0;
+        ksw = ksw < left ? ksw : left;
+    }
     const long long njobs = (long long)ksw * nt;
     const int inner = s_inner;
     const int phase0 = s_phase;
@@ -474,7 +485,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                 const int sw = (int)(j / nt);
                 const int ti = tb + (int)(j - (long long)sw * nt);
                 const int ph = phase_of(MIXED, MIXED ? (phase0 + sw) % inner : 0, inner);
-                const bool fp64 = (ph == PH_P64 || ph == PH_P64R);
+                const bool fp64 = PART == 1 ? true : PART == 2 ? false : (ph == PH_P64 || ph == PH_P64R);
                 unsigned char* st = smem + sidx * L.bytes;
                 const int r0 = __ldg(t.row0 + ti), r1 = __ldg(t.row0 + ti + 1);
                 const int p0 = __ldg(t.nnz0 + ti), p1 = __ldg(t.nnz0 + ti + 1);
@@ -608,7 +619,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
             }
         }
         const int ph = phase_of(MIXED, pos, inner);
-        const bool norm_ph = (ph == PH_P64 || ph == PH_P64R);
+        const bool norm_ph = PART == 1 ? true : PART == 2 ? false : (ph == PH_P64 || ph == PH_P64R);
         double ss = 0.0;
         unsigned long long mx = 0;
         const double* xs = v.x[xb];
@@ -1555,24 +1566,32 @@ cudaError_t launch_row_sweep(int ph, const DevMat& m, const DevVec& v, JacCtl* c
     return cudaGetLastError();
 }
 
-template <int RPT, int STAGES, bool MIXED, int NWM, int LPR = 1, int SYNC = 0>
+template <int RPT, int STAGES, bool MIXED, int NWM, int LPR = 1, int SYNC = 0, int PART = 0>
 static const void* persistent_fn()
 {
-    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED, NWM, LPR, SYNC>);
+    return reinterpret_cast<const void*>(&k_persistent<RPT, STAGES, MIXED, NWM, LPR, SYNC, PART>);
 }
 
-template <int STAGES, bool MIXED, int SYNC>
+template <int STAGES, bool MIXED, int SYNC, int PART = 0>
 static const void* persistent_fn_lanes(int lanes)
 {
     switch (lanes) {
-    case 1: return persistent_fn<1, STAGES, MIXED, 8, 1, SYNC>();
-    case 2: return persistent_fn<1, STAGES, MIXED, 8, 2, SYNC>();
-    case 4: return persistent_fn<1, STAGES, MIXED, 8, 4, SYNC>();
+    case 1: return persistent_fn<1, STAGES, MIXED, 8, 1, SYNC, PART>();
+    case 2: return persistent_fn<1, STAGES, MIXED, 8, 2, SYNC, PART>();
+    case 4: return persistent_fn<1, STAGES, MIXED, 8, 4, SYNC, PART>();
     case 8:
         if constexpr (SYNC == 3) return nullptr;   // split layouts use 1, 2 or 4 lanes
-        else return persistent_fn<1, STAGES, MIXED, 8, 8, SYNC>();
+        else return persistent_fn<1, STAGES, MIXED, 8, 8, SYNC, PART>();
     default: return nullptr;
     }
+}
+
+// The two launches of a mixed cycle (part 1: FP64 pass, 2: FP32 sweeps).
+template <int STAGES>
+static const void* mixed_fn_lanes(int lanes, int part)
+{
+    return part == 1 ? persistent_fn_lanes<STAGES, true, 0, 1>(lanes)
+                     : part == 2 ? persistent_fn_lanes<STAGES, true, 0, 2>(lanes) : nullptr;
 }
 
 // threads = 32 x math warps: 224 -> 7 (2 CTAs/SM, 128 regs),
@@ -1581,8 +1600,9 @@ static const void* persistent_fn_lanes(int lanes)
 // a tile then holds threads / lanes rows.  sync = 0 grid barrier, 1 neighbour
 // flags, 2 asynchronous relaxation (1 and 2: 256 threads, FP64 only), 3 grid
 // barrier over a split interface layout (256 threads, FP64, lanes 1, 2, 4).
-const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, int sync)
+const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, int sync, int part)
 {
+    if (mixed != (part != 0)) return nullptr;   // mixed solves run as split cycles
     if (sync == 3) {
         // grid barrier with a split interface block: FP64, 256 threads, 1/2/4 lanes
         if (mixed || threads != 256 || (lanes != 1 && lanes != 2 && lanes != 4)) return nullptr;
@@ -1609,15 +1629,19 @@ const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, in
     }
     if (sync != 0) return nullptr;
     if (threads == 256 && stages == 3)
-        return mixed ? persistent_fn_lanes<3, true, 0>(lanes) : persistent_fn_lanes<3, false, 0>(lanes);
+        return mixed ? mixed_fn_lanes<3>(lanes, part) : persistent_fn_lanes<3, false, 0>(lanes);
     if (threads == 256 && stages == 2)
-        return mixed ? persistent_fn_lanes<2, true, 0>(lanes) : persistent_fn_lanes<2, false, 0>(lanes);
+        return mixed ? mixed_fn_lanes<2>(lanes, part) : persistent_fn_lanes<2, false, 0>(lanes);
     if (stages != 4) return nullptr;
     if (threads == 256)
-        return mixed ? persistent_fn_lanes<4, true, 0>(lanes) : persistent_fn_lanes<4, false, 0>(lanes);
+        return mixed ? mixed_fn_lanes<4>(lanes, part) : persistent_fn_lanes<4, false, 0>(lanes);
     if (lanes != 1) return nullptr;
-    if (threads == 224) return mixed ? persistent_fn<1, 4, true, 7>() : persistent_fn<1, 4, false, 7>();
-    if (threads == 480) return mixed ? persistent_fn<1, 4, true, 15>() : persistent_fn<1, 4, false, 15>();
+    if (threads == 224)
+        return mixed ? (part == 1 ? persistent_fn<1, 4, true, 7, 1, 0, 1>() : persistent_fn<1, 4, true, 7, 1, 0, 2>())
+                     : persistent_fn<1, 4, false, 7>();
+    if (threads == 480)
+        return mixed ? (part == 1 ? persistent_fn<1, 4, true, 15, 1, 0, 1>() : persistent_fn<1, 4, true, 15, 1, 0, 2>())
+                     : persistent_fn<1, 4, false, 15>();
     return nullptr;
 }
 

@@ -11,7 +11,9 @@ cudaError_t launch_row_sweep(int phase, const DevMat& m, const DevVec& v, JacCtl
 
 // Persistent kernel instance for (rows per tile, pipeline stages, mixed cycle);
 // nullptr if that combination is not compiled.
-const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, int sync);
+// part: 0 for FP64 kernels; mixed kernels come as the two launches of a
+// refinement cycle, 1 = its FP64 residual pass, 2 = its FP32 inner sweeps.
+const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, int sync, int part = 0);
 int persistent_smem_bytes(int rows, int emax, int stages);
 int persistent_threads(int rows);
 const void* halo_kernel(int stages, bool mixed);
