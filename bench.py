@@ -343,7 +343,18 @@ def run_extra(args, local, stream):
             f64 /= 128.0
         t_hbm = (mat_b + vec_b) / (peak * 1e9)
         t_f64 = f64 / FP64_PIPE_PER_S
+        if prec == "fp64":
+            # the oracle's multi-right-hand-side sweep over every system, one global sweep
+            from oracle import oracle as O
+            t0 = time.perf_counter()
+            for A_, b_ in zip(mats, rhs):
+                O.sweep_multi(A_, b_, np.zeros_like(b_))
+            oracle_fields = {"oracle_seconds_per_global_sweep": round(time.perf_counter() - t0, 4),
+                             "oracle_cores": 1}
+        else:
+            oracle_fields = {}
         emit({"extra": "batched_256x4_to_1e-8", "precision": prec, "seconds": round(stt["last_ms"] / 1e3, 4),
+              **oracle_fields,
               "algorithmic_bytes": mat_b + vec_b, "gbs": round(gbs_b, 1),
               "frac_of_measured_hbm": round(gbs_b / peak, 4), "fp64_instr": f64,
               "frac_of_fp64_pipe": round(t_f64 / (stt["last_ms"] * 1e-3), 4),
@@ -398,7 +409,11 @@ def run_extra(args, local, stream):
                                            maxit=400000, nparts=8) - xt) ** 2).item()
     fd = (Lp - Lm) / (2 * h)
     an = float(g @ dirn)
+    from oracle import oracle as O
+    At = O.transpose(A)
+    ofld = _oracle_fields(At, np.ones(A.n), budget_s=1.0)
     emit({"extra": "adjoint_diffusion_96cubed", "forward_seconds": round(t1 - t0, 4),
+          "oracle_us_per_sweep_transposed": ofld["oracle_us_per_sweep"], "oracle_sample_sweeps": ofld["oracle_sample_sweeps"],
           "backward_seconds": round(t2 - t1, 4), "tol": tol, "n": int(A.n), "nnz": int(A.nnz),
           "db_directional_grad": an, "db_central_difference": fd,
           "rel_diff": abs(an - fd) / max(abs(fd), 1e-300)})
