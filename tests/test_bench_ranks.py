@@ -46,3 +46,35 @@ def test_whole_job_rate_over_two_gloo_ranks():
 
 def test_whole_job_rate_without_a_process_group():
     assert bench.whole_job_rate(10.0, 4.0) == (2.5, 4.0, 10.0)
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the CPU oracle on the benchmark's
+    workload) prints exactly one JSON line with the contract's keys."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_roofline_fields_name_the_binding_floor():
+    peak, _ = bench._measured_peak()
+    # memory-bound case: 1 GB, few FP64 instructions
+    f = bench._roofline_fields(1e9, 1e9 / (peak * 1e9) * 1e6 / 0.8, 1e6)
+    assert f["bound"] == "hbm" and f["frac_of_bound"] == pytest.approx(0.8, rel=1e-3)
+    # FP64-bound case: the instructions need longer than the bytes
+    t_f64 = 1e9 / bench.FP64_PIPE_PER_S * 1e6
+    f = bench._roofline_fields(1e6, t_f64 / 0.5, 1e9)
+    assert f["bound"] == "fp64" and f["frac_of_bound"] == pytest.approx(0.5, rel=1e-3)
