@@ -452,6 +452,23 @@ def run_extra(args, local, stream):
             J.jac_free(c)
             emit(line)
 
+    # ---- kernel forms at 160^3 (band-row, 64 bands, fixed geometry, default
+    # balance): one launch per sweep, the persistent pipelined kernel, and
+    # the persistent kernel with each tile's x halo staged in shared memory
+    A = W.laplace7(160)
+    b = W.solution_and_rhs(A, 0)[1]
+    for variant, name in ((1, "one_launch_per_sweep"), (2, "persistent_l2_gather"), (3, "persistent_staged_halo")):
+        c = J.jac_setup(A, b, J.JAC_BANDROW, 64, J.opts(variant=variant, sweeps_per_graph=250,
+                                                         stream=stream.cuda_stream, device=local))
+        J.jac_sweep(c, 250)
+        J.jac_sweep(c, 1000)
+        stt = J.jac_stats(c)
+        us = stt["last_ms"] * 1e3 / 1000
+        emit({"extra": "kernel_forms_160cubed", "variant": variant, "form": name, "us_per_sweep": round(us, 2),
+              "kernel": _geometry(stt)["kernel"], "halo_window_elems": int(stt["halo_window_elems"]),
+              **_roofline_fields(stt["bytes_per_sweep_fp64"], us, _fp64_instr(A.n, A.nnz))})
+        J.jac_free(c)
+
     # ---- split interface block at 160^3, 4x4x4 subdomains: the paper's local
     # matrices and two-step product against node-based substructuring (the
     # interface rows owned once); both autotuned, 2000 sweeps each
