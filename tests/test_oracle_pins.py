@@ -373,3 +373,24 @@ def test_adjoint_gradients_match_dense_reference():
         bm[i] -= h
         fd = (L(dense, bp) - L(dense, bm)) / (2 * h)
         assert fd == pytest.approx(db[i], rel=1e-5, abs=1e-9)
+
+
+@pytest.mark.parametrize("m,seed", [(5, 0), (6, 3)])
+def test_fe27_operator_bound_and_lu_solution(m, seed):
+    """The FE-like 27-point operator has no closed form: pin its structure
+    (symmetric, rows of 8 to 27 entries), the Jacobi bound that its relative
+    dominance margin gives, rho(D^{-1}(L+U)) <= 1/(1+1e-2), and the oracle's
+    converged solve against dense LU."""
+    A = W.fe27_deleted(m, seed=seed)
+    Ad = A.scipy().toarray()
+    assert np.array_equal(Ad, Ad.T)
+    lens = np.diff(A.rowptr)
+    assert lens.min() >= 8 and lens.max() <= 27
+    d = np.diag(Ad)
+    T = np.eye(A.n) - Ad / d[:, None]
+    rho = np.max(np.abs(np.linalg.eigvals(T)))
+    assert rho <= 1.0 / 1.01 + 1e-12
+    xs, b = W.solution_and_rhs(A, seed)
+    x, k, rel, st = O.solve(A, b, None, tol=1e-13, maxit=100000)
+    assert st == O.JO_OK
+    assert np.max(np.abs(x - np.linalg.solve(Ad, b))) <= 1e-11 * np.max(np.abs(xs))
