@@ -244,3 +244,73 @@ def test_unstructured_local_matrices_with_mixed_sign_pieces(lanes):
         assert np.max(np.abs(J.jac_get_x(ctx) - xs)) <= 1e-9 * np.max(np.abs(xs))
     finally:
         J.jac_free(ctx)
+
+
+def _star(nsub, seed):
+    """nsub subdomains, each holding row 0 and one row of its own; row 0
+    is then a group of nsub slot rows."""
+    rng = np.random.default_rng(seed)
+    locs = []
+    for s in range(nsub):
+        a = rng.uniform(0.1, 1.0)
+        locs.append(W.LocalCSR(2, np.array([0, 2, 4], np.int32), np.array([1, 0, 0, 1], np.int32),
+                               np.array([-a, 3.0, -a, 2.0 + a]), np.array([0, s + 1], np.int32)))
+    return locs, nsub + 1
+
+
+def _everything_shared(n, seed):
+    """Two subdomains that both hold every row, each with half of a
+    diagonally dominant tridiagonal matrix: no interior rows at all."""
+    rng = np.random.default_rng(seed)
+    locs = []
+    for s in range(2):
+        rowptr, col, val = [0], [], []
+        for i in range(n):
+            for j in (i - 1, i, i + 1):
+                if 0 <= j < n:
+                    col.append(j)
+                    val.append(2.5 + rng.uniform(0, 0.5) if j == i else -0.5 * rng.uniform(0.5, 1.0))
+            rowptr.append(len(col))
+        locs.append(W.LocalCSR(n, np.array(rowptr, np.int32), np.array(col, np.int32), np.array(val),
+                               np.arange(n, dtype=np.int32)))
+    return locs, n
+
+
+@pytest.mark.parametrize("case", ["one_row", "star32", "star8_lanes4", "everything_shared"])
+def test_split_degenerate_layouts(case):
+    if case == "one_row":
+        locs = [W.LocalCSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]),
+                           np.array([0], np.int32))]
+        n, lanes = 1, 1
+    elif case == "star32":
+        locs, n = _star(32, 1)
+        lanes = 1
+    elif case == "star8_lanes4":
+        locs, n = _star(8, 2)
+        lanes = 4
+    else:
+        locs, n = _everything_shared(700, 3)
+        lanes = 1
+    P = O.split_prepare(locs, n)
+    rng = np.random.default_rng(9)
+    b, x0 = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    ctx = J.jac_setup_local(n, locs, b, J.opts(lanes_per_row=lanes, debug=1))
+    try:
+        st = J.jac_stats(ctx)
+        assert st["interface_rows"] == int((P.mult >= 2).sum())
+        x = x0.copy()
+        J.jac_set_x(ctx, x0)
+        for _ in range(3):
+            y_ref, ss, _ = O.split_sweep(P, b, x)
+            rel = J.jac_sweep(ctx, 1)
+            g = J.jac_get_x(ctx)
+            sc = np.abs(b) + 1.0
+            for L in locs:
+                rows = np.repeat(np.arange(L.n), np.diff(L.rowptr))
+                off = L.col != rows
+                np.add.at(sc, L.l2g[rows[off]], np.abs(L.val[off] * x[L.l2g[L.col[off]]]))
+            assert np.all(np.abs(g - y_ref) <= RTOL * sc / np.abs(P.d))
+            assert abs(rel - np.sqrt(ss) / np.linalg.norm(b)) <= 1e-12 * (np.sqrt(ss) / np.linalg.norm(b)) + 1e-15
+            x = y_ref
+    finally:
+        J.jac_free(ctx)
