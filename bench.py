@@ -434,23 +434,43 @@ def run_extra(args, local, stream):
         line["oracle_seconds_full_solve_estimate"] = round(line["oracle_us_per_sweep"] * 1e-6 * line["iterations"], 3)
         J.jac_free(c)
         emit(line)
-        # the same problem with the interface block split between subdomains
-        # (Sec. 4.3 local matrices); the paper's JSS columns at 8 and 64 processes
-        # use its local stopping rule, this library the global test
-        paper_jss = {33: {8: 699, 64: 525}, 65: {8: 2132, 64: 1889}}
-        for sub in ((2, 2, 2), (4, 4, 4)):
-            S = sub[0] * sub[1] * sub[2]
-            locs = W.cell_box_locals("q1", N, sub)
-            o = J.opts(norm=J.JAC_NORM_INF, sweeps_per_graph=64, autotune=1, stream=stream.cuda_stream, device=local)
-            c = J.jac_setup_local(A.n, locs, b, o)
-            line = _solve_line(J, c, 1e-8, 100000, A, b, None, f"paper_q1_{N}cubed_nodes_split_interface", "fp64",
-                               split=True)
-            line["subdomains"] = S
-            line["iterations"] = line["sweeps"] + 1
-            line["paper_iterations_jss_local_test"] = paper_jss[N][S]
-            line["paper_iterations_global"] = paper[N][0]
-            J.jac_free(c)
-            emit(line)
+        # every splitting at 8 and 64 partitions, next to the paper's JB, JBO and
+        # JSS rows (iterations, communication and total seconds, Sec. 5.2 tables).
+        # The GPU counterpart of the communication time is the CTAs' barrier
+        # wait; the paper's JSS counts come from its local stopping test, this
+        # library keeps the global one.
+        paper_rows = {33: {8: {"JB": (746, 34.5, 35.8), "JBO": (746, 1.5, 3.1), "JSS": (699, 1.4, 3.2)},
+                           64: {"JB": (746, 734.6, 734.7), "JBO": (746, 1.1, 2.1), "JSS": (525, 1.8, 2.4)}},
+                      65: {8: {"JB": (2216, 848.7, 882.7), "JBO": (2216, 14.9, 53.9), "JSS": (2132, 13.7, 48.0)},
+                           64: {"JB": (2216, 7055.0, 7058.6), "JBO": (2216, 5.7, 28.0),
+                                "JSS": (1889, 16.2, 23.0)}}}
+        g = N - 2
+        for P, sub in ((8, (2, 2, 2)), (64, (4, 4, 4))):
+            forms = (("JB", "band-row", lambda o: J.jac_setup(A, b, J.JAC_BANDROW, P, o)),
+                     ("JBO", "band-row balanced by non-zeros", lambda o: J.jac_setup(A, b, J.JAC_BANDROW_NNZ, P, o)),
+                     ("JSS", "substructuring, interface rows owned once",
+                      lambda o: J.jac_setup(A, b, J.JAC_SUBSTRUCT, 0, J.opts(
+                          norm=J.JAC_NORM_INF, sweeps_per_graph=64, autotune=1, grid=(g, g, g), subdomains=sub,
+                          stream=stream.cuda_stream, device=local))),
+                     ("JSS", "substructuring, interface block split between subdomains",
+                      lambda o: J.jac_setup_local(A.n, W.cell_box_locals("q1", N, sub), b, o)))
+            for paper_col, form, make in forms:
+                o = J.opts(norm=J.JAC_NORM_INF, sweeps_per_graph=64, autotune=1, stream=stream.cuda_stream,
+                           device=local)
+                c = make(o)
+                split = form.endswith("split between subdomains")
+                line = _solve_line(J, c, 1e-8, 100000, A, b, None, f"paper_q1_{N}cubed_splittings", "fp64",
+                                   split=split)
+                comp, wait = J.jac_get_trace(c)
+                J.jac_free(c)
+                tot = float(comp.sum() + wait.sum())
+                it, comm_s, total_s = paper_rows[N][P][paper_col]
+                emit({"extra": f"paper_q1_{N}cubed_splittings", "partitions": P, "paper_column": paper_col,
+                      "form": form, "iterations": line["sweeps"] + 1, "seconds": line["seconds"],
+                      "us_per_sweep": line["us_per_sweep"], "barrier_wait_share": round(float(wait.sum()) / tot, 4)
+                      if tot > 0 else None, "kernel": line["kernel"], "paper_iterations": it,
+                      "paper_comm_seconds": comm_s, "paper_total_seconds": total_s,
+                      "paper_hardware": "LISA cluster nodes C1-C6, OpenMPI over Ethernet (Sec. 5.2)"})
 
     # ---- kernel forms at 160^3 (band-row, 64 bands, fixed geometry, default
     # balance): one launch per sweep, the persistent pipelined kernel, and
