@@ -1892,7 +1892,9 @@ jac_status jac_get_batch_results(jac_ctx* c, int64_t* sweeps, double* relres)
 jac_status jac_adjoint_grad(jac_ctx* c, const double* lambda, const double* x, double* dA, int32_t memory)
 {
     if (!c || !lambda || !x || !dA) return c ? fail(c, JAC_EINVAL, "NULL argument") : JAC_EINVAL;
-    if (!c->d_orow) return fail(c, JAC_EINVAL, "jac_adjoint_grad needs the forward (non-transposed) context");
+    if (!c->d_orow)
+        return fail(c, JAC_EINVAL, "jac_adjoint_grad needs a forward jac_setup context (not transposed, batched or "
+                                   "built from local matrices)");
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
     if (!c->d_stage2) CK(c, dalloc(&c->d_stage2, c->n + 16));

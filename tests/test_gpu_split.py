@@ -123,6 +123,11 @@ def test_split_solve_and_set_b():
         J.jac_sweep(ctx, 1)
         P = O.split_prepare(locs, A.n)
         _assert_sweep_close(A, b2, x, J.jac_get_x(ctx), O.split_sweep(P, b2, x)[0])
+        # the adjoint gradient needs the caller's assembled pattern, which a
+        # context built from local matrices does not hold
+        with pytest.raises(J.JacobiError) as ei:
+            J.jac_adjoint_grad(ctx, np.zeros(A.n), np.zeros(A.n), np.zeros(A.nnz))
+        assert ei.value.status == J.JAC_EINVAL and "local matrices" in str(ei.value)
     finally:
         J.jac_free(ctx)
 
