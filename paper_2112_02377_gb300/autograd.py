@@ -38,7 +38,11 @@ class _Handle:
             pass
 
 
-class _Solve(torch.autograd.Function):
+class JacSolve(torch.autograd.Function):
+    """The solve as a torch.autograd.Function:
+    ``JacSolve.apply(val, b, rowptr, col, tol, maxit, nparts, x0, opts)``
+    (``jacobi_solve`` is the keyword-argument form)."""
+
     @staticmethod
     def forward(ctx, val, b, rowptr, col, tol, maxit, nparts, x0, extra):
         n = rowptr.numel() - 1
@@ -91,4 +95,4 @@ def jacobi_solve(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, b: 
     and the adjoint solve (relative 2-norm of the residual); ``x0`` warm-starts
     the forward solve.  Extra keyword arguments are jac_opts fields.
     """
-    return _Solve.apply(val, b, rowptr, col, float(tol), int(maxit), int(nparts), x0, opts)
+    return JacSolve.apply(val, b, rowptr, col, float(tol), int(maxit), int(nparts), x0, opts)
