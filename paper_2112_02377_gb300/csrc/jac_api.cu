@@ -1759,8 +1759,11 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
         if (ha->done != DONE_RUNNING || ha->status != 0) break;
         if (c->batched) {
             // Systems that have stopped leave their CTAs idle while the grid waits
-            // for the rest: once the rows still iterating fall below 70 % of the
+            // for the rest: once the rows still iterating fall below 95 % of the
             // tiled rows, cut tiles over those systems only (between launches).
+            // Measured on GB300, 256 systems x 4 right-hand sides: FP64 2.02 s at
+            // 70 %, 1.87 s at 85 %, 1.84 s at 95 %, 1.91 s at 98 %, 1.93 s when
+            // any system stops (each re-tiling costs a host round trip).
             std::vector<int32_t> mask(c->nsys);
             CK(c, cudaStreamSynchronize(s));
             CK(c, cudaMemcpy(mask.data(), c->d_mask, mask.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -1768,7 +1771,7 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
             int64_t active = 0;
             for (int q = 0; q < c->nsys; ++q)
                 if (mask[q] != all) active += c->h_sys_off[q + 1] - c->h_sys_off[q];
-            if (active > 0 && active * 10 < c->tiled_rows * 7) {
+            if (active > 0 && active * 20 < c->tiled_rows * 19) {
                 st = batched_tile(c, mask);
                 if (st != JAC_OK) { cleanup(); return st; }
             }
