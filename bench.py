@@ -550,8 +550,9 @@ def main():
     ap.add_argument("--profile-variant", type=int, default=0, help="kernel variant of the profiling case (0 = default)")
     ap.add_argument("--profile-rows", type=int, default=0, help="tile rows of the profiling case (0 = default)")
     ap.add_argument("--profile-cps", type=int, default=0, help="CTAs per SM of the profiling case (0 = default)")
-    ap.add_argument("--profile-matrix", default="laplace7", choices=["laplace7", "fe27"],
-                    help="profiling case matrix: the 160^3 7-point system or the 128^3 FE-like 27-point one")
+    ap.add_argument("--profile-matrix", default="laplace7", choices=["laplace7", "fe27", "batched"],
+                    help="profiling case matrix: the 160^3 7-point system, the 128^3 FE-like 27-point one, or "
+                         "the 256 batched 7-point systems with 4 right-hand sides (224-row tiles)")
     ap.add_argument("--profile-lanes", type=int, default=0, help="lanes per row of the profiling case (0 = auto)")
     ap.add_argument("--profile-stages", type=int, default=0, help="pipeline stages of the profiling case (0 = auto)")
     ap.add_argument("--profile-split", action="store_true",
@@ -592,7 +593,12 @@ def main():
                    precision=J.JAC_MIXED if mixed else J.JAC_FP64, inner_sweeps=max(2, K),
                    tile_rows=args.profile_rows, ctas_per_sm=args.profile_cps,
                    lanes_per_row=args.profile_lanes, stages=args.profile_stages)
-        if args.profile_matrix == "fe27":
+        if args.profile_matrix == "batched":
+            mats, rhs = W.laplace7_batch(256, seed=0, nrhs=4)
+            ob = J.opts(nrhs=4, sweeps_per_graph=K, device=local, precision=J.JAC_MIXED if mixed else J.JAC_FP64,
+                        inner_sweeps=max(2, K), tile_rows=224)
+            c = J.jac_setup_batched(mats, rhs, ob)
+        elif args.profile_matrix == "fe27":
             A = W.fe27_deleted(128, seed=0)
             b = W.solution_and_rhs(A, 0)[1]
             c = J.jac_setup(A, b, J.JAC_BANDROW_NNZ, 64, o)
