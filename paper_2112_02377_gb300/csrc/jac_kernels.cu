@@ -116,12 +116,34 @@ __device__ __forceinline__ Real group_sum(Real v)
 
 // A row of an oversized tile (its S and col were not staged), summed by L
 // lanes straight from global memory; kept out of line so that the staged
-// loop's register allocation does not carry it.
+// loop's register allocation does not carry it.  The loads of GCH entries
+// go out together (values and columns, then the gathers) before their FMAs,
+// which still run in stored order: a long row costs a few round trips per
+// GCH entries instead of one per entry.
+constexpr int GCH = 4;
 template <int L, class Real>
 __device__ __noinline__ Real lanes_global(const Real* S, const int* col, const Real* src, int kb, int len, int q,
                                           Real acc)
 {
-    for (int e = kb + q; e < kb + len; e += L) {
+    int e = kb + q;
+    const int end = kb + len;
+    for (; e + (GCH - 1) * L < end; e += GCH * L) {
+        int c[GCH];
+        Real s[GCH], x[GCH];
+#pragma unroll
+        for (int u = 0; u < GCH; ++u) {
+            c[u] = __ldg(col + e + u * L);
+            s[u] = __ldg(S + e + u * L);
+        }
+#pragma unroll
+        for (int u = 0; u < GCH; ++u) x[u] = __ldcg(src + c[u]);
+#pragma unroll
+        for (int u = 0; u < GCH; ++u) {
+            if constexpr (sizeof(Real) == 8) acc = __fma_rn(s[u], x[u], acc);
+            else acc = __fmaf_rn(s[u], x[u], acc);
+        }
+    }
+    for (; e < end; e += L) {
         if constexpr (sizeof(Real) == 8) acc = __fma_rn(__ldg(S + e), __ldcg(src + __ldg(col + e)), acc);
         else acc = __fmaf_rn(__ldg(S + e), __ldcg(src + __ldg(col + e)), acc);
     }
