@@ -389,7 +389,7 @@ jac_status get_graph(jac_ctx* c, bool mixed, cudaGraphExec_t* out)
 jac_status run_graph(jac_ctx* c, bool mixed)
 {
     if (c->no_graph) return enqueue_step(c, mixed);
-    cudaGraphExec_t g;
+    cudaGraphExec_t g = nullptr;
     jac_status st = get_graph(c, mixed, &g);
     if (st != JAC_OK) {
         // Stream capture of this launch form is unavailable: launch directly.
