@@ -1,5 +1,6 @@
-// Host-side checks of the split interface layout (make_split_form) and of the
-// tiler's warp alignment (make_tiling), without a GPU.  Builds random local
+// Host-side checks of the tiler (make_tiling: partitions, caps, CTA ranges),
+// of the split interface layout (make_split_form) and of the tiler's warp
+// alignment for it, without a GPU.  Builds random local
 // matrices over overlapping node sets, lays them out for several warp row
 // counts and verifies every invariant the sweep kernel relies on.  Prints
 // "ok" and returns 0, or prints the first violation and returns 1.
@@ -149,8 +150,68 @@ static int check_case(int64_t n, int nsub, int max_extra, int warp_rows)
     return 0;
 }
 
+// General tiling (make_plan / make_scaled_form / make_tiling on a CSR with
+// irregular rows, some longer than a tile's entry cap).
+static int check_tiling(int64_t n, jac_splitting sp, int32_t nparts, int32_t rows_per_tile, int32_t max_entries,
+                        int64_t ctas)
+{
+    HostCSR M;
+    M.n = n;
+    M.rowptr.assign(1, 0);
+    for (int64_t r = 0; r < n; ++r) {
+        int64_t len = 1 + (int64_t)(next_u64() % 12);
+        if (next_u64() % 500 == 0) len = 2 * max_entries + (int64_t)(next_u64() % 100);   // oversized
+        for (int64_t k = 0; k < len && k < n - 1; ++k) {
+            int64_t c = (int64_t)(next_u64() % n);
+            if (c == r) c = (c + 1) % n;
+            M.col.push_back((int32_t)c);
+            M.val.push_back(-0.01);
+        }
+        M.col.push_back((int32_t)r);
+        M.val.push_back(100.0);
+        M.rowptr.push_back((int32_t)M.col.size());
+    }
+    jac_opts o{};   // band splittings read no option (node_of_row NULL: row r at node r)
+    Plan plan;
+    Error e = make_plan(M, sp, nparts, o, plan);
+    CHECK(e.ok(), "make_plan: %s", e.msg.c_str());
+    ScaledForm tf;
+    e = make_scaled_form(M, plan, tf);
+    CHECK(e.ok(), "make_scaled_form: %s", e.msg.c_str());
+    Tiling t;
+    make_tiling(tf, plan, rows_per_tile, max_entries, ctas, t, nullptr);
+    CHECK((int64_t)t.cta0.size() == ctas + 1 && t.cta0[0] == 0 && t.cta0[ctas] == t.ntiles(), "CTA ranges");
+    for (int64_t g = 0; g < ctas; ++g) CHECK(t.cta0[g + 1] >= t.cta0[g], "CTA ranges not monotone");
+    CHECK(t.row0.front() == 0 && t.row0.back() == n, "tiles do not cover the rows");
+    size_t p = 0;
+    for (int64_t i = 0; i < t.ntiles(); ++i) {
+        const int64_t r0 = t.row0[i], r1 = t.row0[i + 1];
+        CHECK(r1 > r0 && r1 - r0 <= rows_per_tile, "tile rows %lld", (long long)(r1 - r0));
+        while (p + 1 < plan.part_ptr.size() && plan.part_ptr[p + 1] <= r0) ++p;
+        CHECK(r1 <= plan.part_ptr[p + 1], "tile crosses a partition");
+        const int64_t ent = tf.rowptr[r1] - tf.rowptr[r0];
+        CHECK(ent <= max_entries || r1 - r0 == 1, "tile of %lld rows holds %lld entries", (long long)(r1 - r0),
+              (long long)ent);
+        CHECK(t.nnz0[i] == tf.rowptr[r0], "entry offset");
+    }
+    return 0;
+}
+
 int main()
 {
+    for (int trial = 0; trial < 8; ++trial) {
+        const int64_t n = 1000 + (int64_t)(next_u64() % 20000);
+        const jac_splitting sp = trial % 2 ? JAC_BANDROW_NNZ : JAC_BANDROW;
+        const int32_t nparts = 1 + (int32_t)(next_u64() % 64);
+        const int32_t rows = trial % 3 == 0 ? 128 : 256;
+        const int32_t cap = 300 + (int32_t)(next_u64() % 2000);
+        const int64_t ctas = 1 + (int64_t)(next_u64() % 456);
+        if (check_tiling(n, sp, nparts, rows, cap, ctas)) {
+            std::printf("  (tiling trial %d, n %lld, parts %d, rows %d, cap %d, ctas %lld)\n", trial, (long long)n,
+                        nparts, rows, cap, (long long)ctas);
+            return 1;
+        }
+    }
     const int warp_rows[] = {32, 16, 8};
     for (int trial = 0; trial < 12; ++trial)
         for (int w : warp_rows) {
