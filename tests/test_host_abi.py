@@ -180,6 +180,28 @@ def test_autotune_rejects_a_fixed_geometry_before_touching_the_gpu():
     assert "autotune" in str(e.value)
 
 
+@pytest.mark.parametrize("case,msg", [
+    ("nrhs3", "nrhs must be 1, 2 or 4"),
+    ("no_systems", "nsys"),
+    ("stages5", "stages"),
+    ("sync7", "sync"),
+])
+def test_batched_inputs_are_checked_before_any_device_call(case, msg):
+    A = W.laplace7(4)
+    As, bs, o = [A], [np.ones(A.n)], J.opts()
+    if case == "nrhs3":
+        o = J.opts(nrhs=3)
+    elif case == "no_systems":
+        As, bs = [], []
+    elif case == "stages5":
+        o = J.opts(stages=5)
+    elif case == "sync7":
+        o = J.opts(sync=7)
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup_batched(As, bs, o)
+    assert ei.value.status == J.JAC_EINVAL and msg in str(ei.value)
+
+
 def test_empty_system_is_rejected():
     E = W.CSR(0, np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32), np.zeros(0))
     with pytest.raises(J.JacobiError) as ei:
