@@ -49,3 +49,34 @@ def test_ctypes_structures_match_the_header(tmp_path):
             desc = getattr(cls, fname)
             assert (desc.offset, desc.size) == (off, size), f"{cname}.{fname}"
             assert ctypes.sizeof(ftype) == size, f"{cname}.{fname}"
+
+
+def _header_prototypes():
+    import re
+    s = open(os.path.join(ROOT, "include", "jacobi.h")).read()
+    s = re.sub(r"/\*.*?\*/", "", s, flags=re.S)
+    out = {}
+    for m in re.finditer(r"(?m)^([a-z_0-9 ]+\**)\s*\b(jac_[a-z_]+)\s*\(([^)]*)\)\s*;", s):
+        params = [" ".join(p.split()) for p in m.group(3).split(",")]
+        out[m.group(2)] = (" ".join(m.group(1).split()), params)
+    return out
+
+
+def _ctype_of(decl: str):
+    if "*" in decl:
+        return ctypes.c_void_p
+    base = decl.split()[-2] if len(decl.split()) > 1 else decl
+    return {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double,
+            "jac_splitting": ctypes.c_int32, "jac_status": ctypes.c_int32}[base]
+
+
+def test_ctypes_signatures_match_the_header():
+    protos = _header_prototypes()
+    L = J.lib()
+    assert sorted(protos) == sorted(J.EXPORTED)
+    for name, (ret, params) in protos.items():
+        f = getattr(L, name)
+        want_ret = {"void": None, "jac_status": ctypes.c_int32, "const char*": ctypes.c_char_p}[ret]
+        assert f.restype == want_ret, name
+        want_args = [_ctype_of(p) for p in params]
+        assert list(f.argtypes) == want_args, name
