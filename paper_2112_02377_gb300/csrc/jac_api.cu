@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <new>
+#include <stdexcept>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -154,6 +156,32 @@ jac_status fail(jac_ctx* c, jac_status st, const std::string& msg)
 {
     if (c) c->err = msg;
     else g_setup_error = msg;
+    return st;
+}
+
+// Host code throws only when an allocation fails (std::bad_alloc from a
+// std::vector, std::length_error for a size past its maximum).  No exception
+// may cross the C ABI, so every entry point that returns a status is a
+// function-try-block whose handler turns the exception into JAC_ENOMEM (any
+// other exception into JAC_EINVAL) and records the message.
+jac_status host_exception(jac_ctx* c) noexcept
+{
+    jac_status st = JAC_EINVAL;
+    const char* m = "unexpected host exception";
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        st = JAC_ENOMEM;
+        m = "host allocation failed";
+    } catch (const std::length_error&) {
+        st = JAC_ENOMEM;
+        m = "host allocation too large";
+    } catch (...) {
+    }
+    try {
+        fail(c, st, m);
+    } catch (...) {
+    }
     return st;
 }
 
@@ -740,7 +768,7 @@ void jac_free(jac_ctx* ctx) { destroy(ctx); }
 
 jac_status jac_partition_plan(const jac_csr* A, jac_splitting s, int32_t nparts, const jac_opts* o_in,
                               int64_t* perm, int64_t* part_ptr, int64_t* nparts_out)
-{
+try {
     jac_opts o;
     jac_opts_default(&o);
     if (o_in) o = *o_in;
@@ -756,11 +784,13 @@ jac_status jac_partition_plan(const jac_csr* A, jac_splitting s, int32_t nparts,
     for (int64_t p = 0; p <= plan.nparts(); ++p) part_ptr[p] = plan.part_ptr[p];
     if (nparts_out) *nparts_out = plan.nparts();
     return JAC_OK;
+} catch (...) {
+    return host_exception(nullptr);
 }
 
 jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t nparts, const jac_opts* o_in,
                                 int64_t* recv_ptr, int32_t* recv_from, int64_t* recv, int64_t* total)
-{
+try {
     jac_opts o;
     jac_opts_default(&o);
     if (o_in) o = *o_in;
@@ -782,6 +812,8 @@ jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t npart
     }
     *total = (int64_t)rc.size();
     return JAC_OK;
+} catch (...) {
+    return host_exception(nullptr);
 }
 
 inline int64_t nnz_off_of(const ScaledForm& tf) { return tf.rowptr.empty() ? 0 : tf.rowptr.back(); }
@@ -1237,7 +1269,7 @@ static jac_status tune(const jac_opts& o, const std::vector<Geometry>& cand, con
 
 jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, const jac_opts* o_in,
                      jac_ctx** out)
-{
+try {
     if (!out) return fail(nullptr, JAC_EINVAL, "out is NULL");
     *out = nullptr;
     jac_opts o;
@@ -1288,11 +1320,13 @@ jac_status jac_setup(const jac_csr* A, const double* b, jac_splitting s, int32_t
     return tune(o, cand, [&](const jac_opts& oc, const std::vector<double>* rc, jac_ctx** pc) {
         return setup_single(A, b, s, nparts, oc, rc, pc);
     }, out);
+} catch (...) {
+    return host_exception(nullptr);
 }
 
 jac_status jac_setup_local(int64_t n, int32_t nsub, const jac_local* sub, const double* b, const jac_opts* o_in,
                            jac_ctx** out)
-{
+try {
     if (!out) return fail(nullptr, JAC_EINVAL, "out is NULL");
     *out = nullptr;
     jac_opts o;
@@ -1370,11 +1404,13 @@ jac_status jac_setup_local(int64_t n, int32_t nsub, const jac_local* sub, const 
         }
     }
     return tune(o, cand, make, out);
+} catch (...) {
+    return host_exception(nullptr);
 }
 
 jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const* b, const jac_opts* o_in,
                              jac_ctx** out)
-{
+try {
     if (!out) return fail(nullptr, JAC_EINVAL, "out is NULL");
     *out = nullptr;
     jac_opts o;
@@ -1592,10 +1628,12 @@ jac_status jac_setup_batched(int32_t nsys, const jac_csr* A, const double* const
     CK(nullptr, sm ? cudaStreamSynchronize(sm) : cudaDeviceSynchronize());
     *out = c.release();
     return JAC_OK;
+} catch (...) {
+    return host_exception(nullptr);
 }
 
 jac_status jac_set_x(jac_ctx* c, const double* x, int32_t memory)
-{
+try {
     if (!c) return JAC_EINVAL;
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
@@ -1626,10 +1664,12 @@ jac_status jac_set_x(jac_ctx* c, const double* x, int32_t memory)
     CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
     c->sweeps_total = 0;
     return JAC_OK;
+} catch (...) {
+    return host_exception(c);
 }
 
 jac_status jac_set_b(jac_ctx* c, const double* b, int32_t memory)
-{
+try {
     if (!c) return JAC_EINVAL;
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
@@ -1651,10 +1691,12 @@ jac_status jac_set_b(jac_ctx* c, const double* b, int32_t memory)
                           (int)c->n, c->d_ctl, s));
     CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
     return JAC_OK;
+} catch (...) {
+    return host_exception(c);
 }
 
 jac_status jac_sweep(jac_ctx* c, int32_t k, double* relres_out)
-{
+try {
     if (!c) return JAC_EINVAL;
     if (k < 0) return fail(c, JAC_EINVAL, "k must be >= 0");
     if (k == 0) {
@@ -1689,12 +1731,14 @@ jac_status jac_sweep(jac_ctx* c, int32_t k, double* relres_out)
     if (relres_out) *relres_out = h.relres;
     if (!c->canaries.empty()) return check_canaries(c);
     return JAC_OK;
+} catch (...) {
+    return host_exception(c);
 }
 
 static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out, double* relres_out);
 
 jac_status jac_solve(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out, double* relres_out)
-{
+try {
     if (!c) return JAC_EINVAL;
     if (c->sync != JAC_SYNC_ASYNC || c->precision != JAC_FP64 || c->batched)
         return solve_impl(c, tol, maxit, sweeps_out, relres_out);
@@ -1709,6 +1753,9 @@ jac_status jac_solve(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out,
     c->certify = false;
     c->last_ms += ms_async;
     return st;
+} catch (...) {
+    if (c) c->certify = false;
+    return host_exception(c);
 }
 
 static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* sweeps_out, double* relres_out)
@@ -1838,7 +1885,7 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
 }
 
 jac_status jac_get_x(jac_ctx* c, double* x, int32_t memory)
-{
+try {
     if (!c || !x) return c ? fail(c, JAC_EINVAL, "x is NULL") : JAC_EINVAL;
     DeviceGuard g(c->device);
     cudaStream_t s = stream_of(c);
@@ -1862,10 +1909,12 @@ jac_status jac_get_x(jac_ctx* c, double* x, int32_t memory)
     }
     CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
     return JAC_OK;
+} catch (...) {
+    return host_exception(c);
 }
 
 jac_status jac_get_history(jac_ctx* c, double* out, int64_t max, int64_t* count)
-{
+try {
     if (!c || !count) return JAC_EINVAL;
     const int64_t have = std::min<int64_t>(c->h_ctl[0].evals, c->hist_cap);
     const int64_t m = std::min<int64_t>(have, std::max<int64_t>(max, 0));
@@ -1875,10 +1924,12 @@ jac_status jac_get_history(jac_ctx* c, double* out, int64_t max, int64_t* count)
     }
     *count = out ? m : have;
     return JAC_OK;
+} catch (...) {
+    return host_exception(c);
 }
 
 jac_status jac_get_batch_results(jac_ctx* c, int64_t* sweeps, double* relres)
-{
+try {
     if (!c) return JAC_EINVAL;
     if (!c->batched) {
         if (sweeps) sweeps[0] = c->h_ctl[0].k;
@@ -1894,10 +1945,12 @@ jac_status jac_get_batch_results(jac_ctx* c, int64_t* sweeps, double* relres)
     }
     if (relres) CK(c, cudaMemcpy(relres, c->d_rel, cnt * sizeof(double), cudaMemcpyDeviceToHost));
     return JAC_OK;
+} catch (...) {
+    return host_exception(c);
 }
 
 jac_status jac_adjoint_grad(jac_ctx* c, const double* lambda, const double* x, double* dA, int32_t memory)
-{
+try {
     if (!c || !lambda || !x || !dA) return c ? fail(c, JAC_EINVAL, "NULL argument") : JAC_EINVAL;
     if (!c->d_orow)
         return fail(c, JAC_EINVAL, "jac_adjoint_grad needs a forward jac_setup context (not transposed, batched or "
@@ -1915,10 +1968,12 @@ jac_status jac_adjoint_grad(jac_ctx* c, const double* lambda, const double* x, d
                           memory == JAC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
     return JAC_OK;
+} catch (...) {
+    return host_exception(c);
 }
 
 jac_status jac_get_trace(jac_ctx* c, double* compute_ms, double* wait_ms, int64_t max, int64_t* ctas)
-{
+try {
     if (!c || !ctas) return JAC_EINVAL;
     *ctas = c->d_trace ? c->grid : 0;
     if (!c->d_trace || max <= 0) return JAC_OK;
@@ -1931,10 +1986,12 @@ jac_status jac_get_trace(jac_ctx* c, double* compute_ms, double* wait_ms, int64_
         if (wait_ms) wait_ms[i] = h[4 * i + 1] * 1e-6;
     }
     return JAC_OK;
+} catch (...) {
+    return host_exception(c);
 }
 
 jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
-{
+try {
     if (!c || !out) return JAC_EINVAL;
     std::memset(out, 0, sizeof(*out));
     const JacCtl& h = c->h_ctl[0];
@@ -1970,6 +2027,8 @@ jac_status jac_stats(jac_ctx* c, jac_stats_t* out)
     out->stages = c->variant >= 2 ? c->stages : 0;
     out->ctas_per_sm = (c->variant >= 2 && c->n > 0 && c->grid > 0) ? c->grid / std::max(1, c->sms) : 0;
     return JAC_OK;
+} catch (...) {
+    return host_exception(c);
 }
 
 }  // extern "C"
