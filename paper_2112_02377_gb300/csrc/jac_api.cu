@@ -159,11 +159,22 @@ jac_status fail(jac_ctx* c, jac_status st, const std::string& msg)
     return st;
 }
 
+jac_status cuda_fail(jac_ctx* c, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? JAC_ENOMEM : JAC_ECUDA, m);
+}
+
+}  // namespace
+
+namespace jac {
+
 // Host code throws only when an allocation fails (std::bad_alloc from a
 // std::vector, std::length_error for a size past its maximum).  No exception
 // may cross the C ABI, so every entry point that returns a status is a
 // function-try-block whose handler turns the exception into JAC_ENOMEM (any
-// other exception into JAC_EINVAL) and records the message.
+// other exception into JAC_EINVAL) and records the message.  Call it only
+// from a catch handler.
 jac_status host_exception(jac_ctx* c) noexcept
 {
     jac_status st = JAC_EINVAL;
@@ -185,11 +196,9 @@ jac_status host_exception(jac_ctx* c) noexcept
     return st;
 }
 
-jac_status cuda_fail(jac_ctx* c, cudaError_t e, const char* what)
-{
-    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
-    return fail(c, e == cudaErrorMemoryAllocation ? JAC_ENOMEM : JAC_ECUDA, m);
-}
+}  // namespace jac
+
+namespace {
 
 #define CK(ctx, call)                                                   \
     do {                                                                \

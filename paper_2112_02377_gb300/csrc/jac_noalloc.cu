@@ -30,6 +30,7 @@
 
 namespace jac {
 void record_thread_error(const std::string& msg);   // jac_api.cu
+jac_status host_exception(jac_ctx* c) noexcept;    // jac_api.cu
 }
 
 namespace {
@@ -145,7 +146,7 @@ jac_status fail(jac_status st, const std::string& m)
 extern "C" jac_status jac_sweep_noalloc(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                                         const double* b, const double* x_in, double* x_out, int32_t k,
                                         double* relres_out, void* stream)
-{
+try {
     if (n < 1) return fail(JAC_EINVAL, "jac_sweep_noalloc: n must be >= 1");
     if (n > kMaxRows)
         return fail(JAC_EINVAL, "jac_sweep_noalloc: n exceeds the fixed scratch limit of 4194304 rows");
@@ -202,4 +203,7 @@ extern "C" jac_status jac_sweep_noalloc(int64_t n, const int32_t* rowptr, const 
         if (relres_out) *relres_out = h.bb > 0.0 ? std::sqrt(h.ss) / std::sqrt(h.bb) : std::sqrt(h.ss);
     }
     return JAC_OK;
+} catch (...) {
+    // an error message that could not be allocated, or a failed mutex lock
+    return jac::host_exception(nullptr);
 }

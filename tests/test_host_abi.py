@@ -319,3 +319,22 @@ def test_split_interface_setup_without_a_gpu_fails_loudly():
     with pytest.raises(J.JacobiError) as ei:
         J.jac_setup_local(216, locs, np.ones(216))
     assert ei.value.status == J.JAC_ECUDA
+
+
+def test_noalloc_entry_point_checks_arguments_and_reports_a_missing_device():
+    """jac_sweep_noalloc rejects bad sizes before any device call and, with no
+    GPU, returns JAC_ECUDA with a message (it never throws or crashes)."""
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: host pointers would reach the kernels")
+    L = J.lib()
+    A = W.laplace7(4)
+    rp, cl, vl = A.rowptr.astype(np.int32), A.col.astype(np.int32), A.val.astype(np.float64)
+    b, x0, out = np.ones(A.n), np.zeros(A.n), np.zeros(A.n)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rel = ctypes.c_double()
+    st = L.jac_sweep_noalloc(0, P(rp), P(cl), P(vl), P(b), P(x0), P(out), 1, ctypes.byref(rel), None)
+    assert st == J.JAC_EINVAL and b"n must be" in L.jac_last_error(None)
+    st = L.jac_sweep_noalloc(A.n, P(rp), P(cl), P(vl), P(b), P(x0), P(out), 1, ctypes.byref(rel), None)
+    assert st == J.JAC_ECUDA and L.jac_last_error(None).startswith(b"jac_sweep_noalloc: ")
