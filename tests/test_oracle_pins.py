@@ -272,6 +272,44 @@ def test_sweeps_to_1e6_on_16cubed_seed0():
         assert cf[want] <= 1e-6 < cf[want - 1]
 
 
+def _dst_crossing(grid, xstar, tol):
+    """First k with closed-form relres_k <= tol (bisection; the history is
+    monotone for the 7-point Laplacian, whose Jacobi eigenvalues have |mu| < 1),
+    with the relative margins of relres_k and relres_{k-1} from tol."""
+    gx, gy, gz = grid
+    z = F.dstn(xstar.reshape(gz, gy, gx), type=1, norm="ortho")
+    ev = [2.0 - 2.0 * np.cos(np.pi * np.arange(1, g + 1) / (g + 1)) for g in (gz, gy, gx)]
+    lam = ev[0][:, None, None] + ev[1][None, :, None] + ev[2][None, None, :]
+    w = (lam * z) ** 2
+    lmu2 = 2.0 * np.log(np.abs(1.0 - lam / 6.0))
+    bn = np.sqrt(np.sum(w))
+    rel = lambda k: np.sqrt(np.sum(w * np.exp(k * lmu2))) / bn
+    lo, hi = 0, 1
+    while rel(hi) > tol:
+        lo, hi = hi, hi * 2
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        lo, hi = (lo, mid) if rel(mid) <= tol else (mid, hi)
+    return hi, 1.0 - rel(hi) / tol, rel(hi - 1) / tol - 1.0
+
+
+def test_160cubed_benchmark_workload_closed_form_and_oracle_sweeps():
+    """The benchmark's 160^3 system (numpy seed 0): the closed form reaches
+    relres 1e-8 after 42,745 sweeps, with a margin far above rounding on both
+    sides of the crossing, so an FP64 solve must stop there exactly; the oracle's
+    first sweeps at this size follow the closed form."""
+    grid = (160, 160, 160)
+    A = W.laplace7(160)
+    xs, b = W.solution_and_rhs(A, 0)
+    k, below, above = _dst_crossing(grid, xs, 1e-8)
+    assert k == 42745
+    assert below > 1e-5 and above > 1e-5
+    x, kk, rel, st, hist = O.solve(A, b, tol=1e-8, maxit=6, history=True)
+    assert st == O.JO_ENOTCONV and len(hist) == 7
+    cf = _dst_history(grid, xs, 7)
+    assert np.all(np.abs(hist - cf) <= 1e-12 * cf)
+
+
 def test_asymptotic_contraction_is_spectral_radius():
     """Late residual contraction equals rho(I - D^{-1}A) = cos(pi/(m+1))
     (Sec. 3, convergence theorem; the rate bound (rho+eps)^k)."""
