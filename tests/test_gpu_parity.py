@@ -737,3 +737,26 @@ def test_full_size_fe27_128cubed_per_sweep_parity():
             x = xg
     finally:
         J.jac_free(ctx)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "async"])
+def test_full_size_fe27_128cubed_solve_reaches_1e10(mode):
+    """The FE-27 benchmark's solves at full size (2.1 M rows, 53.8 M entries)
+    in its configuration (autotuned, nnz-balanced bands, graphs of 256 sweeps,
+    mixed cycles of 128): each reports relres <= 1e-10, and the residual of the
+    returned iterate recomputed on the host agrees with it to 1e-3 relative
+    (the host's rounding floor is near 1e-15 here)."""
+    A = W.fe27_deleted(128, seed=0)
+    xs, b = W.solution_and_rhs(A, 0)
+    prec = J.JAC_MIXED if mode == "mixed" else J.JAC_FP64
+    sync = J.JAC_SYNC_ASYNC if mode == "async" else J.JAC_SYNC_GRID
+    ctx = _setup(A, b, "bandrow_nnz", 64, autotune=1, precision=prec, sync=sync, inner_sweeps=128,
+                 sweeps_per_graph=256)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-10, 200000)
+        assert st == J.JAC_OK and 0 < rel <= 1e-10
+        x = J.jac_get_x(ctx)
+    finally:
+        J.jac_free(ctx)
+    relx = np.linalg.norm(b - A.scipy() @ x) / np.linalg.norm(b)
+    assert abs(relx - rel) <= 1e-3 * rel
