@@ -10,6 +10,10 @@ gradient g = dL/dx back to the inputs:
 
 (differentiating A x = b gives A dx = db - dA x).  Both solves and the
 gradient kernel run in the CUDA library; this module only marshals tensors.
+
+A forward or adjoint solve that reaches maxit before tol raises
+JacobiError(JAC_ENOTCONV): an unconverged x (or lambda) would give a loss
+and gradients of a different problem, so neither is returned.
 """
 from __future__ import annotations
 
@@ -51,7 +55,7 @@ class JacSolve(torch.autograd.Function):
         try:
             if x0 is not None:
                 J.jac_set_x(fwd, x0)
-            k, rel, st = J.jac_solve(fwd, tol, maxit)
+            k, rel, st = J.jac_solve(fwd, tol, maxit, raise_on_notconv=True)
             x = torch.empty(n, dtype=torch.float64, device=b.device)
             J.jac_get_x(fwd, x)
         except Exception:
@@ -72,7 +76,7 @@ class JacSolve(torch.autograd.Function):
         o = J.opts(transpose=1, **extra)
         adj = J.jac_setup((rowptr, col, val), gx, J.JAC_BANDROW, nparts, o)
         try:
-            J.jac_solve(adj, tol, maxit)
+            J.jac_solve(adj, tol, maxit, raise_on_notconv=True)
             lam = torch.empty(n, dtype=torch.float64, device=gx.device)
             J.jac_get_x(adj, lam)
         finally:

@@ -110,3 +110,27 @@ def test_full_size_96cubed_adjoint_properties():
     assert np.linalg.norm(g - S.T @ lam) <= 1e-11 * np.linalg.norm(g)
     rowid = np.repeat(np.arange(A.n), np.diff(A.rowptr))
     assert np.array_equal(dval, -(lam[rowid] * x[A.col]))
+
+
+def test_unconverged_forward_or_adjoint_solve_raises():
+    """A solve that reaches maxit before tol must not hand back an unconverged
+    x, lambda or gradient: both the forward and the adjoint solve raise
+    JAC_ENOTCONV."""
+    from paper_2112_02377_gb300 import jacobi as J
+    A = W.diffusion7(8, seed=5)
+    rng = np.random.default_rng(2)
+    b = rng.uniform(-1, 1, A.n)
+    rp, cl = _t(A.rowptr), _t(A.col)
+    val = _t(A.val).requires_grad_(True)
+    bt = _t(b).requires_grad_(True)
+    with pytest.raises(J.JacobiError) as ei:
+        jacobi_solve(rp, cl, val, bt, tol=1e-12, maxit=3)
+    assert ei.value.status == J.JAC_ENOTCONV
+    # the forward solve starts at the LU solution (its test passes at k = 0);
+    # the adjoint solve starts at 0 and cannot reach 1e-12 in 3 sweeps
+    xr = np.linalg.solve(A.scipy().toarray(), b)
+    x = jacobi_solve(rp, cl, val, bt, tol=1e-12, maxit=3, x0=_t(xr))
+    L = torch.sum(x ** 2)
+    with pytest.raises(J.JacobiError) as ei:
+        L.backward()
+    assert ei.value.status == J.JAC_ENOTCONV
