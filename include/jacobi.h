@@ -391,9 +391,19 @@ jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t npart
  * a memory pool that owns the device, loops that must not stall on the device
  * synchronisation cudaMalloc/cudaFree imply, or host applications that forbid
  * allocation after start-up.  It uses only the caller's buffers and a fixed
- * scratch area compiled into the library (JAC_NOALLOC_SCRATCH_BYTES, held on
- * every GPU that loads the library until the process exits); it calls no
- * allocator, the CUDA runtime's or any library's.
+ * scratch area compiled into the library (JAC_NOALLOC_SCRATCH_BYTES: a vector
+ * of JAC_NOALLOC_MAX_ROWS doubles plus the reduction slots).  Once a call is
+ * set up in a CUDA context, it calls no allocator, the CUDA runtime's or any
+ * library's, on the device or the host (only a failing call builds an error
+ * message on the host).
+ *
+ * Set-up: the first call in each CUDA context (per device for runtime-API
+ * callers; again after cudaDeviceReset, which replaces the context) looks the
+ * scratch area's device address up.  Under CUDA's default lazy module loading
+ * this look-up is also when the library's device code is loaded into that
+ * context and the scratch area's device memory is committed there, once,
+ * until the context is destroyed.  Make that first call before any stream
+ * capture, and where committing memory later is not acceptable.
  *   n          rows, 1 <= n <= JAC_NOALLOC_MAX_ROWS (larger n: JAC_EINVAL).
  *   rowptr, col, val   0-based CSR of A in device memory, diagonal stored in
  *              every row (a zero or missing diagonal returns JAC_ENUMERIC).
@@ -404,14 +414,14 @@ jac_status jac_dependency_lists(const jac_csr* A, jac_splitting s, int32_t npart
  *   stream     cudaStream_t (NULL = legacy default stream); the call
  *              synchronises it before returning.
  * Each sweep computes x'_i = (b_i - sum_{j != i} a_ij x_j) / a_ii with one
- * launch, as the one-launch-per-sweep variant does.  The first call on a
- * device looks up the scratch area's device address (make it before any
- * stream capture).  All calls share the scratch area: calls whose work
- * overlaps on the GPU race.  Errors: JAC_EINVAL, JAC_ENUMERIC, JAC_ECUDA;
- * jac_last_error(NULL) describes the last failure on this thread.
+ * launch, as the one-launch-per-sweep variant does.  All calls share the
+ * scratch area, which keeps the last call's contents (each call clears what
+ * must start at zero): calls whose work overlaps on the GPU race.
+ * Errors: JAC_EINVAL, JAC_ENUMERIC, JAC_ECUDA; jac_last_error(NULL)
+ * describes the last failure on this thread.
  */
 #define JAC_NOALLOC_MAX_ROWS 4194304
-#define JAC_NOALLOC_SCRATCH_BYTES 33816640
+#define JAC_NOALLOC_SCRATCH_BYTES 33947712
 jac_status jac_sweep_noalloc(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                              const double* b, const double* x_in, double* x_out, int32_t k,
                              double* relres_out, void* stream);
