@@ -1786,13 +1786,22 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
     // step's control block is inspected on the host.
     JacCtl* ha = &c->h_ctl[0];
     JacCtl* hb = &c->h_ctl[1];
-    cudaEvent_t ea = nullptr, eb = nullptr;
-    CK(c, cudaEventCreateWithFlags(&ea, cudaEventDisableTiming));
-    CK(c, cudaEventCreateWithFlags(&eb, cudaEventDisableTiming));
-    auto cleanup = [&]() { cudaEventDestroy(ea); cudaEventDestroy(eb); };
+    // the two events are destroyed on every return path
+    struct EventPair {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~EventPair()
+        {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    CK(c, cudaEventCreateWithFlags(&ev.a, cudaEventDisableTiming));
+    CK(c, cudaEventCreateWithFlags(&ev.b, cudaEventDisableTiming));
+    cudaEvent_t& ea = ev.a;
+    cudaEvent_t& eb = ev.b;
     st = run_graph(c, mixed);
     if (st == JAC_OK) st = fetch_ctl(c, ha);
-    if (st != JAC_OK) { cleanup(); return st; }
+    if (st != JAC_OK) return st;
     cudaEventRecord(ea, s);
     long long last_k = -1;
     int stalled = 0;
@@ -1807,15 +1816,14 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
     for (;;) {
         if (++steps > step_cap) {
             cudaStreamSynchronize(s);
-            cleanup();
             return fail(c, JAC_ECUDA, "the sweep loop did not terminate within its step bound");
         }
         st = run_graph(c, mixed);
         if (st == JAC_OK) st = fetch_ctl(c, hb);
-        if (st != JAC_OK) { cleanup(); return st; }
+        if (st != JAC_OK) return st;
         cudaEventRecord(eb, s);
         cudaError_t e = cudaEventSynchronize(ea);
-        if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "solve loop"); }
+        if (e != cudaSuccess) return cuda_fail(c, e, "solve loop");
         if (ha->done != DONE_RUNNING || ha->status != 0) break;
         if (c->batched) {
             // Systems that have stopped leave their CTAs idle while the grid waits
@@ -1833,14 +1841,13 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
                 if (mask[q] != all) active += c->h_sys_off[q + 1] - c->h_sys_off[q];
             if (active > 0 && active * 20 < c->tiled_rows * 19) {
                 st = batched_tile(c, mask);
-                if (st != JAC_OK) { cleanup(); return st; }
+                if (st != JAC_OK) return st;
             }
         }
         const long long prog = ha->k * 4 + ha->phase + ha->evals;
         if (prog == last_k) {
             if (++stalled > 4) {
                 cudaStreamSynchronize(s);
-                cleanup();
                 return fail(c, JAC_ECUDA, "the sweep loop made no progress");
             }
         } else {
@@ -1852,7 +1859,6 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
     }
     CK(c, cudaEventRecord(c->ev1, s));
     cudaError_t e = cudaEventSynchronize(eb);
-    cleanup();
     if (e != cudaSuccess) return cuda_fail(c, e, "solve loop");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
