@@ -7,6 +7,7 @@
 #include <map>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -601,30 +602,53 @@ jac_status check_opts(const jac_opts& o, jac_ctx* err_ctx)
 
 // ---------------------------------------------------------------- autotuner
 
-// Device time per sweep of a freshly set-up context: a warm-up, then a timed
-// call (FP64: fixed sweeps; mixed: two refinement cycles of a solve that
-// cannot converge).  The iterate is reset to x^0 = 0 afterwards.
+// Device time per sweep of a freshly set-up context: a warm-up, then the
+// median of three timed calls, each long enough (about 2 ms of device time or
+// more) that launch and clock noise stay small next to the differences
+// between geometries.  FP64: fixed sweeps; mixed: whole refinement cycles of a
+// solve that cannot converge.  The iterate is reset to x^0 = 0 afterwards.
+// A call that fails (e.g. a divergent iteration overflowing) ends the timing
+// with what was measured so far.
 double time_per_sweep(jac_ctx* c)
 {
-    double ms = 1e30;
+    constexpr double kTargetMs = 2.0;
+    std::vector<double> t;
+    double warm = 1e30;
     if (c->precision == JAC_MIXED && !c->batched) {
-        // two refinement cycles, timed twice (the faster counts): a single short
-        // timing has been seen to pick a geometry 2.6x slower than the best
         int64_t k = 0;
         double rel = 0.0;
-        const int64_t cyc = 2 * (int64_t)c->o.inner_sweeps;
-        jac_solve(c, 0.0, cyc - 1, &k, &rel);
-        for (int rep = 0; rep < 2; ++rep) {
+        const int64_t inner = std::max<int64_t>(2, c->o.inner_sweeps);
+        const int64_t cyc = 2 * inner;
+        jac_status st = jac_solve(c, 0.0, cyc - 1, &k, &rel);
+        if ((st == JAC_OK || st == JAC_ENOTCONV) && k > 0) warm = c->last_ms / (double)k;
+        const int64_t ncyc = std::min<int64_t>(
+            64, std::max<int64_t>(2, (int64_t)std::ceil(kTargetMs / std::max(warm * inner, 1e-6))));
+        for (int rep = 0; rep < 3; ++rep) {
             jac_set_x(c, nullptr, JAC_MEM_HOST);
-            const jac_status st = jac_solve(c, 0.0, cyc - 1, &k, &rel);
-            if ((st == JAC_OK || st == JAC_ENOTCONV) && k >= cyc - 1) ms = std::min(ms, c->last_ms / (double)k);
+            st = jac_solve(c, 0.0, ncyc * inner - 1, &k, &rel);
+            if ((st != JAC_OK && st != JAC_ENOTCONV) || k < ncyc * inner - 1) break;
+            t.push_back(c->last_ms / (double)k);
         }
     } else {
         double rel = 0.0;
-        if (jac_sweep(c, 8, &rel) == JAC_OK && jac_sweep(c, 32, &rel) == JAC_OK) ms = c->last_ms / 32.0;
+        if (jac_sweep(c, 8, &rel) == JAC_OK) warm = c->last_ms / 8.0;
+        const int nsw = (int)std::min<double>(8192.0, std::max(32.0, std::ceil(kTargetMs / std::max(warm, 1e-6))));
+        for (int rep = 0; rep < 3; ++rep) {
+            if (jac_sweep(c, nsw, &rel) != JAC_OK) break;
+            t.push_back(c->last_ms / (double)nsw);
+        }
     }
     jac_set_x(c, nullptr, JAC_MEM_HOST);
-    return ms;
+    if (t.empty()) return warm;
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
+}
+
+// JAC_AUTOTUNE_LOG=1 in the environment: one line per timed candidate on stderr.
+static bool autotune_log()
+{
+    const char* v = std::getenv("JAC_AUTOTUNE_LOG");
+    return v && v[0] == '1';
 }
 
 struct Geometry {
@@ -1209,14 +1233,24 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
 // of each on this matrix and keep the fastest; then re-cut its CTA row ranges
 // from the measured per-CTA compute times while that keeps paying.
 using MakeCtx = std::function<jac_status(const jac_opts&, const std::vector<double>*, jac_ctx**)>;
+//
+// cand[0] is the cost model's prior (the geometry the row lengths point to).
+// Another candidate replaces it only if it is more than 5 % faster, so that
+// two geometries within timing noise of each other do not swap from one
+// set-up to the next.
 static jac_status tune(const jac_opts& o, const std::vector<Geometry>& cand, const MakeCtx& make, jac_ctx** out)
 {
     const bool async = (o.sync == JAC_SYNC_ASYNC);
+    const bool log = autotune_log();
     jac_ctx* best = nullptr;
     jac_opts best_o = o;
     double best_ms = 1e30;
+    jac_ctx* prior = nullptr;
+    jac_opts prior_o = o;
+    double prior_ms = 1e30;
     std::string first_err;
-    for (const Geometry& g : cand) {
+    for (size_t gi = 0; gi < cand.size(); ++gi) {
+        const Geometry& g = cand[gi];
         jac_opts o2 = o;
         o2.autotune = 0;
         o2.variant = g.variant;
@@ -1233,7 +1267,16 @@ static jac_status tune(const jac_opts& o, const std::vector<Geometry>& cand, con
             continue;
         }
         const double ms = time_per_sweep(c);
-        if (ms < best_ms) {
+        if (log)
+            std::fprintf(stderr, "autotune: variant %d rows %d ctas/SM %d lanes %d sync %d stages %d: %.3f us/sweep%s\n",
+                         c->variant, c->rows_per_tile, c->grid / std::max(1, c->sms), c->lanes, c->sync, c->stages,
+                         ms * 1e3,
+                         gi == 0 ? " (prior)" : "");
+        if (gi == 0) {
+            prior = c;
+            prior_o = o2;
+            prior_ms = ms;
+        } else if (ms < best_ms) {
             if (best) jac_free(best);
             best = c;
             best_o = o2;
@@ -1241,6 +1284,14 @@ static jac_status tune(const jac_opts& o, const std::vector<Geometry>& cand, con
         } else {
             jac_free(c);
         }
+    }
+    if (prior && (!best || !(best_ms < 0.95 * prior_ms))) {
+        if (best) jac_free(best);
+        best = prior;
+        best_o = prior_o;
+        best_ms = prior_ms;
+    } else if (prior) {
+        jac_free(prior);
     }
     if (!best) return fail(nullptr, JAC_EINVAL, "autotune: no kernel geometry could be set up: " + first_err);
     // Balance calibration: the sweep waits for the slowest CTA, so scale the
@@ -1291,40 +1342,58 @@ try {
     if (o.variant || o.tile_rows || o.ctas_per_sm)
         return fail(nullptr, JAC_EINVAL, "autotune needs variant = tile_rows = ctas_per_sm = 0");
     const bool async = (o.sync == JAC_SYNC_ASYNC);
-    std::vector<Geometry> cand = {{2, 256, 2, 0}, {2, 256, 3, 0}};
-    // asynchronous relaxation runs in the 256-thread geometry only
-    if (!async) {
-        cand.push_back({2, 224, 0, 0});
-        cand.push_back({2, 480, 0, 0});
-        cand.push_back({3, 256, 0, 0});
-    }
-    if (o.precision == JAC_FP64 && !async) {
-        cand.push_back({2, 256, 2, 0, JAC_SYNC_NEIGHBOUR});
-        cand.push_back({2, 256, 3, 0, JAC_SYNC_NEIGHBOUR});
-    }
-    if (o.lanes_per_row == 0) {
-        // the lane counts next to the automatic one (its own arithmetic: see jac_opts.lanes_per_row)
+    // the automatic lane count (its own arithmetic: see jac_opts.lanes_per_row)
+    int la = o.lanes_per_row;
+    if (la == 0) {
         jac_ctx* probe = nullptr;
         jac_opts op = o;
         op.autotune = 0;
         op.variant = 2;
         op.tile_rows = 256;
         if (setup_single(A, b, s, nparts, op, nullptr, &probe) == JAC_OK) {
-            const int la = probe->lanes;
+            la = probe->lanes;
             jac_free(probe);
-            for (int L : {la / 2, la * 2})
-                if (L >= 1 && L <= 8) {
-                    cand.push_back({2, 256, 2, L});
-                    cand.push_back({2, 256, 3, L});
-                }
-            // long rows: larger stages hold whole tiles of 256/L rows
-            if (la >= 2)
-                for (int L : {la, la * 2})
-                    if (L <= 8) {
-                        cand.push_back({2, 256, 2, L, JAC_SYNC_GRID, 3});
-                        cand.push_back({2, 256, 2, L, JAC_SYNC_GRID, 2});
-                    }
         }
+    }
+    // The cost model's prior: one lane per row with 3 CTAs/SM and 3 stages
+    // (short rows, FP64-pipe and gather bound); long rows (2+ lanes) with
+    // 2 CTAs/SM and 2 large stages that hold whole tiles of 256/L rows.
+    std::vector<Geometry> cand;
+    if (la >= 2 && !async) cand.push_back({2, 256, 2, 0, JAC_SYNC_GRID, 2});
+    else cand.push_back({2, 256, 3, 0});
+    auto add = [&](const Geometry& g) {
+        for (const Geometry& h : cand)
+            if (h.variant == g.variant && h.rows == g.rows && h.ctas == g.ctas && h.lanes == g.lanes &&
+                h.sync == g.sync && h.stages == g.stages)
+                return;
+        cand.push_back(g);
+    };
+    add({2, 256, 2, 0});
+    add({2, 256, 3, 0});
+    // asynchronous relaxation runs in the 256-thread geometry only
+    if (!async) {
+        add({2, 224, 0, 0});
+        add({2, 480, 0, 0});
+        add({3, 256, 0, 0});
+    }
+    if (o.precision == JAC_FP64 && !async) {
+        add({2, 256, 2, 0, JAC_SYNC_NEIGHBOUR});
+        add({2, 256, 3, 0, JAC_SYNC_NEIGHBOUR});
+    }
+    if (o.lanes_per_row == 0 && la >= 1) {
+        // the lane counts next to the automatic one
+        for (int L : {la / 2, la * 2})
+            if (L >= 1 && L <= 8) {
+                add({2, 256, 2, L});
+                add({2, 256, 3, L});
+            }
+        // long rows: larger stages hold whole tiles of 256/L rows
+        if (la >= 2)
+            for (int L : {la, la * 2})
+                if (L <= 8) {
+                    add({2, 256, 2, L == la ? 0 : L, JAC_SYNC_GRID, 3});
+                    add({2, 256, 2, L == la ? 0 : L, JAC_SYNC_GRID, 2});
+                }
     }
     return tune(o, cand, [&](const jac_opts& oc, const std::vector<double>* rc, jac_ctx** pc) {
         return setup_single(A, b, s, nparts, oc, rc, pc);
@@ -1402,14 +1471,23 @@ try {
         return setup_core(f->plan, f->tf, n, f->nnz_local, f->partials, f, nullptr, b, JAC_MEM_HOST, o2, dev, rc, pc);
     };
     if (!o.autotune) return make(o, nullptr, out);
+    // prior first (the rule of jac_setup's autotuner), then every geometry of each lane count
+    const int Lp = o.lanes_per_row ? o.lanes_per_row : L0;
     std::vector<Geometry> cand;
+    if (Lp >= 2) cand.push_back({2, 256, 2, Lp, JAC_SYNC_GRID, 2});
+    else cand.push_back({2, 256, 3, Lp});
+    auto add = [&](const Geometry& g) {
+        for (const Geometry& h : cand)
+            if (h.ctas == g.ctas && h.lanes == g.lanes && h.stages == g.stages) return;
+        cand.push_back(g);
+    };
     for (int L : lanes_ok) {
         if (o.lanes_per_row && L != o.lanes_per_row) continue;
-        cand.push_back({2, 256, 2, L});
-        cand.push_back({2, 256, 3, L});
+        add({2, 256, 2, L});
+        add({2, 256, 3, L});
         if (L >= 2) {
-            cand.push_back({2, 256, 2, L, JAC_SYNC_GRID, 3});
-            cand.push_back({2, 256, 2, L, JAC_SYNC_GRID, 2});
+            add({2, 256, 2, L, JAC_SYNC_GRID, 3});
+            add({2, 256, 2, L, JAC_SYNC_GRID, 2});
         }
     }
     return tune(o, cand, make, out);
@@ -1440,7 +1518,11 @@ try {
                 continue;
             }
             const double ms = time_per_sweep(c);
-            if (ms < best_ms) {
+            if (autotune_log())
+                std::fprintf(stderr, "autotune (batched): rows %d: %.3f us/sweep%s\n", rows, ms * 1e3,
+                             rows == 224 ? " (prior)" : "");
+            // 224-row tiles are the prior; 96-row tiles must be more than 5 % faster
+            if (!best || ms < 0.95 * best_ms) {
                 if (best) jac_free(best);
                 best = c;
                 best_ms = ms;
