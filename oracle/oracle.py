@@ -30,6 +30,10 @@ partitioned procedures"):
   the interface block split between subdomains (Sec. 4.3): local matrices
   A_s with A33 = sum_s A33^(s), the two-step product (local sums, then
   assembly at the interface) and the weighted interface dot product.
+* ``band_row_sets`` / ``box_row_sets`` / ``solve_local`` -- stopping on
+  local convergence (Sec. 3, the parallel form of Algorithm 1): every
+  partition tests the residual of the rows it holds (its band, or the nodes
+  of its box of cells under substructuring).
 * ``adjoint_gradients``   -- dL/db = lambda, dL/dA_ij = -lambda_i x_j with
   A^T lambda = dL/dx, the lambda solve done by the same Jacobi loop.
 
@@ -441,6 +445,95 @@ def split_solve(P: _Split, b: np.ndarray, x0: Optional[np.ndarray] = None, tol: 
 # ---------------------------------------------------------------------------
 # Adjoint (gradients through the solve)
 # ---------------------------------------------------------------------------
+
+# ---------------------------------------------------------------------------
+# Stopping on local convergence (Sec. 3, the parallel form of Algorithm 1)
+# ---------------------------------------------------------------------------
+
+def band_row_sets(part_ptr: np.ndarray) -> List[np.ndarray]:
+    """Rows each band-row partition holds (Sec. 4.2): its band, in the
+    original numbering (band splittings do not reorder rows)."""
+    pp = np.asarray(part_ptr, dtype=np.int64)
+    return [np.arange(pp[q], pp[q + 1], dtype=np.int64) for q in range(len(pp) - 1)]
+
+
+def box_row_sets(grid: Sequence[int], sub: Sequence[int], n: int,
+                 node: Optional[np.ndarray] = None) -> List[np.ndarray]:
+    """Rows each subdomain of the geometric substructuring holds (Sec. 4.3):
+    the nodes of its box of grid cells, i.e. its interior nodes and the
+    interface nodes on its box's boundary.
+
+    Built from the cells: along an axis of g nodes cut into p parts (cut node
+    planes c_t = floor(t g / p), t = 1..p-1), the cells have lower corners
+    -1..g-1 (the outer layer touches the Dirichlet boundary) and box t holds
+    the cells whose lower corner lies in [c_t, c_{t+1}) with c_0 = -1 and
+    c_p = g; a node belongs to a box when it is a corner of one of its cells.
+    Returns one array of rows (ascending) per subdomain
+    s = sx + px (sy + py sz)."""
+    gx, gy, gz = (int(v) for v in grid)
+    px, py, pz = (int(v) for v in sub)
+    nodes = np.arange(n, dtype=np.int64) if node is None else np.asarray(node, dtype=np.int64)
+    row_of = np.full(gx * gy * gz, -1, dtype=np.int64)
+    row_of[nodes] = np.arange(n, dtype=np.int64)
+
+    def cell_ranges(g, p):
+        c = [-1] + [(t * g) // p for t in range(1, p)] + [g]
+        return [(c[t], c[t + 1]) for t in range(p)]
+
+    out = []
+    for sz, (z0, z1) in enumerate(cell_ranges(gz, pz)):
+        for sy, (y0, y1) in enumerate(cell_ranges(gy, py)):
+            for sx, (x0, x1) in enumerate(cell_ranges(gx, px)):
+                keep = set()
+                for cz in range(z0, z1):
+                    for cy in range(y0, y1):
+                        for cx in range(x0, x1):
+                            for dz in (0, 1):
+                                for dy in (0, 1):
+                                    for dx in (0, 1):
+                                        i, j, k = cx + dx, cy + dy, cz + dz
+                                        if 0 <= i < gx and 0 <= j < gy and 0 <= k < gz:
+                                            r = row_of[i + gx * (j + gy * k)]
+                                            if r >= 0:
+                                                keep.add(int(r))
+                out.append(np.array(sorted(keep), dtype=np.int64))
+    return out
+
+
+def solve_local(A, b: np.ndarray, sets: Sequence[np.ndarray], x0: Optional[np.ndarray] = None,
+                tol: float = 1e-8, maxit: int = 100000, rule: str = "first"):
+    """Algorithm 1 with the convergence test made per partition.
+
+    Partition p's local test at iterate x^k is max_{i in sets[p]} |r_i| <= tol
+    with r = b - A x^k (the experiments' infinity-norm criterion, Sec. 5.2,
+    restricted to the rows the partition holds).  rule "all": stop at the
+    first k at which every partition passes at once (with the infinity norm
+    this is the global test); rule "first": stop at the first k at which some
+    partition passes.  Sets must be non-empty.
+
+    Returns (x_k, k, p, local_p, status): p is the lowest-numbered partition
+    with the smallest local value at the stopping iterate (rule "first") or
+    the one with the largest (rule "all"), local_p that value; status as in
+    ``solve``."""
+    M = _mat(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(M.n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    sets = [np.asarray(S, dtype=np.int64) for S in sets]
+    if not sets or any(len(S) == 0 for S in sets):
+        raise ValueError("every partition must hold rows")
+    k = 0
+    while True:
+        y, ss, mx, r = sweep(M, b, x, want_r=True)
+        loc = np.array([np.max(np.abs(r[S])) for S in sets])
+        loc = np.where(np.isnan(loc), np.inf, loc)
+        p = int(np.argmin(loc)) if rule == "first" else int(np.argmax(loc))
+        if loc[p] <= tol:
+            return x, k, p, float(loc[p]), JO_OK
+        if k >= maxit:
+            return x, k, p, float(loc[p]), JO_ENOTCONV
+        x = y
+        k += 1
+
 
 def transpose(A):
     """A^T in CSR (rows of A^T keep ascending column order)."""
