@@ -86,6 +86,27 @@ typedef enum {
                                 jac_sweep runs k passes and returns the estimate. */
 } jac_sync;
 
+/* How a solve decides that it has converged (jac_opts.stop). */
+typedef enum {
+    JAC_STOP_GLOBAL = 0,     /* the test value of the whole residual (jac_opts.norm) <= tol.  With
+                                JAC_NORM_INF this is also the paper's "simultaneous local
+                                convergence of all the processors" (Sec. 3): every partition's
+                                local infinity-norm test passing at once is the global one. */
+    JAC_STOP_LOCAL = 1       /* stopping on local convergence, under the reading that the run ends
+                                at the first sweep in which one partition is locally converged:
+                                partition p holds a set of rows R_p and passes when
+                                max_{i in R_p} |r_i| <= tol.  R_p is band p for the band
+                                splittings; under substructuring it is the nodes of subdomain p's
+                                box of grid cells, i.e. its interior and the interface nodes on
+                                its box's boundary (Sec. 4.3), so an interface node is held by
+                                2, 4 or 8 subdomains.  The paper's substructuring counts fall as
+                                subdomains are added (Sec. 5.2 tables), which no test that needs
+                                every partition at once can do.  Needs jac_setup, JAC_FP64,
+                                JAC_NORM_INF, JAC_SYNC_GRID, variant 0 or 2 with 256-thread tiles
+                                and 1, 2 or 4 lanes per row; jac_stats reports the partition that
+                                passed and its local value. */
+} jac_stop;
+
 /* Square sparse matrix in CSR form (Sec. 4.1: AA = val, JA = col, IA = rowptr).
  * rowptr has n+1 entries, rowptr[0] == index_base, rowptr[n] == nnz + index_base;
  * col/val have nnz entries; index_base is 0 or 1 (the paper prints 1-based
@@ -148,6 +169,7 @@ typedef struct {
     int32_t fault_skip_cta;    /* test hook: this CTA never arrives at the grid barrier,
                                   so the others time out (-1 = off) */
     int32_t device;            /* CUDA device ordinal; -1 = the current device */
+    int32_t stop;              /* jac_stop (default JAC_STOP_GLOBAL) */
 } jac_opts;
 
 /* Statistics of a context (jac_stats). */
@@ -175,6 +197,11 @@ typedef struct {
     int32_t lanes_per_row;           /* lanes per row in use (a tile holds tile_rows / lanes_per_row rows) */
     int32_t sync;                    /* jac_sync in use for FP64 sweeps */
     int32_t stages;                  /* pipeline stages of the persistent kernels */
+    int32_t stop;                    /* jac_stop in use */
+    int32_t stop_part;               /* JAC_STOP_LOCAL: the partition whose local test ended the last
+                                        solve (band index, or subdomain s = sx + px (sy + py sz));
+                                        -1 if it did not end on a local test */
+    double stop_local;               /* its local test value max_{i in R_p} |r_i| */
 } jac_stats_t;
 
 /* Defaults for every option. */

@@ -54,6 +54,11 @@ struct JacCtl {
     double relres, res2, resinf;
     double* hist;             // optional history (device), hist_cap entries
     long long hist_cap;
+    // stopping on local convergence: the row set whose test ended the solve
+    // (-1: none) and its value max |r_i| over that set
+    int loc_part;
+    int loc_pad;
+    double loc_val;
 };
 
 struct Partial {
@@ -80,6 +85,11 @@ struct DevMat {
     // kernel rows; d and the iterate the n rows.
     int n_own;
     const unsigned* slot_info;   // per slot row: (interface index << 6) | group size at a group's first row
+    // Stopping on local convergence: the row sets of the partitions' local
+    // tests as a CSR over the rows (row r belongs to sets mem_part[mem_ptr[r]
+    // .. mem_ptr[r+1])); NULL otherwise.
+    const int* mem_ptr;
+    const int* mem_part;
 };
 
 struct DevVec {
@@ -91,6 +101,10 @@ struct DevVec {
     Partial* dec;             // [4] grid-wide sums of sweep j in slot j mod 4 (neighbour sync)
     int nslots;
     unsigned long long* trace;  // [ctas][4]: compute ns, barrier-wait ns, sweeps, 0 (persistent kernels)
+    // stopping on local convergence: [3][nloc] per-set max abs_key(r_i); the
+    // residual of iterate k goes to slot k mod 3
+    unsigned long long* loc;
+    int nloc;
 };
 
 struct DevTiles {
@@ -178,6 +192,68 @@ __device__ __forceinline__ void accumulate_residual(double ynew, double yold, do
     const double r = __dadd_rn(ynew, -yold);
     ss = __fma_rn(r, r, ss);
     mx = umax64(mx, abs_key(r));
+}
+
+// As accumulate_residual, also returning the row's order key abs_key(r).
+__device__ __forceinline__ unsigned long long accumulate_residual_key(double ynew, double yold, double& ss,
+                                                                      unsigned long long& mx)
+{
+    const double r = __dadd_rn(ynew, -yold);
+    ss = __fma_rn(r, r, ss);
+    const unsigned long long key = abs_key(r);
+    mx = umax64(mx, key);
+    return key;
+}
+
+// Stopping on local convergence, called by all 32 lanes of a warp: every
+// lane with a row (row >= 0) raises the maxima of the row sets holding it to
+// the row's key.  A warp whose rows all lie in one set and no other (the
+// common case) makes one atomic; otherwise each row makes one per set.  The
+// maxima are integer keys, so the result does not depend on the order.
+__device__ __forceinline__ void local_sets_update(unsigned long long* slot, const int* mem_ptr, const int* mem_part,
+                                                  int row, unsigned long long key)
+{
+    const bool has = row >= 0;
+    int mb = 0, me = 0, p = -1;
+    if (has) {
+        mb = __ldg(mem_ptr + row);
+        me = __ldg(mem_ptr + row + 1);
+        p = me > mb ? __ldg(mem_part + mb) : -1;
+    }
+    const unsigned act = __ballot_sync(0xffffffffu, has);
+    if (!act) return;
+    const int src = __ffs(act) - 1;
+    const int p0 = __shfl_sync(0xffffffffu, p, src);
+    const bool uniform = __all_sync(0xffffffffu, !has || (me - mb == 1 && p == p0));
+    if (uniform && p0 >= 0) {
+        const unsigned long long wk = warp_max(has ? key : 0ull);
+        if ((threadIdx.x & 31) == 0) atomicMax(slot + p0, wk);
+    } else if (has) {
+        for (int e = mb; e < me; ++e) atomicMax(slot + __ldg(mem_part + e), key);
+    }
+}
+
+// The smallest set maximum of a slot and the lowest set index holding it,
+// by one warp (all lanes get the result).  Exact integer keys: every CTA
+// computing it from the same slot gets the same answer.
+__device__ __forceinline__ void local_sets_min(const unsigned long long* slot, int nloc, unsigned long long& kmin,
+                                               int& pmin)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long k = ~0ull;
+    int p = 0x7fffffff;
+    for (int i = lane; i < nloc; i += 32) {
+        const unsigned long long v = __ldcg(slot + i);
+        if (v < k) { k = v; p = i; }
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
+        const int p2 = __shfl_xor_sync(0xffffffffu, p, o);
+        if (k2 < k || (k2 == k && p2 < p)) { k = k2; p = p2; }
+    }
+    kmin = k;
+    pmin = p;
 }
 
 // Phase of a sweep: plain FP64 sweeps, or position `pos` in the mixed

@@ -409,6 +409,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     constexpr bool NS = (SYNC == 1);      // neighbour-synchronised sweeps
     constexpr bool ASYNC = (SYNC == 2);   // asynchronous (chaotic) relaxation
     constexpr bool SPLIT = (SYNC == 3);   // grid barrier; rows from n_own on are slot rows of a split interface
+    constexpr bool LOC = (SYNC == 4);     // grid barrier; the test also ends on one partition's local test
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int CT = NWM * 32, NW = NWM, ROWS = CT * RPT / LPR;
     // 7 or 15 math warps have 128 registers: software-pipeline the x gathers of
@@ -419,6 +420,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     static_assert(!NS || (!MIXED && !PIPE), "neighbour sync is built for the plain FP64 loop");
     static_assert(!ASYNC || (!MIXED && !PIPE), "asynchronous relaxation is built for the plain FP64 loop");
     static_assert(!SPLIT || (!MIXED && !PIPE), "the split interface block is built for the plain FP64 loop");
+    static_assert(!LOC || (!MIXED && !PIPE), "local stopping is built for the plain FP64 loop");
     const StageLayout L = stage_layout(ROWS, t.emax);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes);
     uint64_t* empty = full + STAGES;
@@ -428,6 +430,8 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     __shared__ int s_xb, s_phase, s_inner, s_test, s_done, s_start, s_skip, s_fail, s_dec_done, s_last, s_stopj;
     __shared__ volatile int s_stop;
     __shared__ double s_relres, s_res2, s_resinf;
+    __shared__ int s_locpart;
+    __shared__ double s_locval;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -453,6 +457,8 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         s_res2 = c->res2;
         s_resinf = c->resinf;
         s_keval = c->k_eval;
+        s_locpart = -1;
+        s_locval = 0.0;
         s_stop = 0;
         s_fail = 0;
         if (fits) {
@@ -644,6 +650,19 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         const bool norm_ph = PART == 1 ? true : PART == 2 ? false : (ph == PH_P64 || ph == PH_P64R);
         double ss = 0.0;
         unsigned long long mx = 0;
+        // local sets: iterate k's maxima go to slot k mod 3; CTA 0 clears slot
+        // (k+1) mod 3 now -- every CTA read it (as slot k-2) before arriving at
+        // the barrier of sweep k-1, and it is written after the barrier of
+        // sweep k, which CTA 0 reaches after these stores
+        unsigned long long* lslot = nullptr;
+        if constexpr (LOC) {
+            lslot = v.loc + (size_t)(k % 3) * v.nloc;
+            if (blockIdx.x == 0 && warp == 0) {
+                unsigned long long* nx = v.loc + (size_t)((k + 1) % 3) * v.nloc;
+                for (int i = lane; i < v.nloc; i += 32) __stcg(nx + i, 0ull);
+                __threadfence();
+            }
+        }
         const double* xs = v.x[xb];
         double* xd = ASYNC ? v.x[xb] : v.x[next_buf(xb)];   // asynchronous: in place
         const float* es = v.e[pos & 1];
@@ -758,7 +777,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                 bool ok = wait_full(jc);
                 // the tile body shuffles across the warp (row groups, interface
                 // groups): after a timeout every lane must skip it together
-                if constexpr (SPLIT || LPR > 1) ok = __all_sync(0xffffffffu, ok);
+                if constexpr (SPLIT || LPR > 1 || LOC) ok = __all_sync(0xffffffffu, ok);
                 if (ok) {
                     const unsigned char* st = smem + sidx * L.bytes;
                     const int* hdr = reinterpret_cast<const int*>(st);
@@ -784,6 +803,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                         else if (in)
                             acc = lanes_global<LPR>(m.S64, m.col, xs, kb, len, q, acc);
                         acc = group_sum<LPR>(acc);
+                        [[maybe_unused]] unsigned long long lkey = 0;
                         if (lead && own) {
                             if (ph == PH_P64) {
                                 __stcg(xd + r, acc);
@@ -792,8 +812,10 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                                 __stcg(v.dlt + r, dl);
                                 __stcg(v.e[1] + r, dl);
                             }
-                            accumulate_residual(acc, xi, ss, mx);
+                            if constexpr (LOC) lkey = accumulate_residual_key(acc, xi, ss, mx);
+                            else accumulate_residual(acc, xi, ss, mx);
                         }
+                        if constexpr (LOC) local_sets_update(lslot, m.mem_ptr, m.mem_part, (lead && own) ? r : -1, lkey);
                         if constexpr (SPLIT) {
                             if (r0 >= m.n_own) {          // a tile of slot rows (tiles never mix the two)
                                 const unsigned info = lead ? __ldg(m.slot_info + (r - m.n_own)) : 0u;
@@ -945,6 +967,9 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                 double tss;
                 unsigned long long tmx;
                 reduce_partials_warp(v.part + (sw & 1) * v.nslots, gridDim.x, tss, tmx);
+                unsigned long long lk = ~0ull;
+                int lp = -1;
+                if constexpr (LOC) local_sets_min(lslot, v.nloc, lk, lp);
                 if (lane == 0) {
                     const Decision d = decide(s_test, ctl->tol, s_klim, ctl->norm_kind, ctl->bnorm, tss, tmx, k);
                     s_relres = d.relres;
@@ -952,6 +977,15 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                     s_resinf = d.resinf;
                     s_keval = k;
                     s_dec_done = d.done;
+                    if constexpr (LOC) {
+                        // one partition's local test ends the solve (the global
+                        // test passing implies it; NaN keys never pass)
+                        if (s_test && !d.numeric_bad && lp >= 0 && lk <= KEY_INF && abs_from_key(lk) <= ctl->tol) {
+                            s_dec_done = DONE_CONVERGED;
+                            s_locpart = lp;
+                            s_locval = abs_from_key(lk);
+                        }
+                    }
                     if (d.numeric_bad && blockIdx.x == 0) atomicOr(&ctl->status, ST_NUMERIC);
                     if (blockIdx.x == 0 && ctl->hist && evals < ctl->hist_cap) ctl->hist[evals] = d.relres;
                 }
@@ -1012,6 +1046,10 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
         ctl->res2 = s_res2;
         ctl->resinf = s_resinf;
         ctl->k_eval = s_keval;
+        if constexpr (LOC) {
+            ctl->loc_part = s_locpart;
+            ctl->loc_val = s_locval;
+        }
         __threadfence();
     }
 }
@@ -1550,6 +1588,8 @@ __global__ void k_arm(JacCtl* ctl, int test, int mixed, int inner, long long k_l
     c->hist_cap = hist_cap;
     c->timeout = timeout;
     c->fault_skip_cta = skip;
+    c->loc_part = -1;
+    c->loc_val = 0.0;
 }
 
 __global__ void k_reset_iterate(JacCtl* ctl)
@@ -1602,7 +1642,7 @@ static const void* persistent_fn_lanes(int lanes)
     case 2: return persistent_fn<1, STAGES, MIXED, 8, 2, SYNC, PART>();
     case 4: return persistent_fn<1, STAGES, MIXED, 8, 4, SYNC, PART>();
     case 8:
-        if constexpr (SYNC == 3) return nullptr;   // split layouts use 1, 2 or 4 lanes
+        if constexpr (SYNC >= 3) return nullptr;   // split layouts and local stopping use 1, 2 or 4 lanes
         else return persistent_fn<1, STAGES, MIXED, 8, 8, SYNC, PART>();
     default: return nullptr;
     }
@@ -1621,7 +1661,8 @@ static const void* mixed_fn_lanes(int lanes, int part)
 // 480 -> 15 (1 CTA/SM, 128 regs).  lanes = lanes per row (256 threads only);
 // a tile then holds threads / lanes rows.  sync = 0 grid barrier, 1 neighbour
 // flags, 2 asynchronous relaxation (1 and 2: 256 threads, FP64 only), 3 grid
-// barrier over a split interface layout (256 threads, FP64, lanes 1, 2, 4).
+// barrier over a split interface layout (256 threads, FP64, lanes 1, 2, 4),
+// 4 grid barrier with the local stopping tests (256 threads, FP64, lanes 1, 2, 4).
 const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, int sync, int part)
 {
     if (mixed != (part != 0)) return nullptr;   // mixed solves run as split cycles
@@ -1632,6 +1673,16 @@ const void* persistent_kernel(int threads, int stages, bool mixed, int lanes, in
         case 2: return persistent_fn_lanes<2, false, 3>(lanes);
         case 3: return persistent_fn_lanes<3, false, 3>(lanes);
         case 4: return persistent_fn_lanes<4, false, 3>(lanes);
+        default: return nullptr;
+        }
+    }
+    if (sync == 4) {
+        // grid barrier with local stopping tests: FP64, 256 threads, 1/2/4 lanes
+        if (mixed || threads != 256 || (lanes != 1 && lanes != 2 && lanes != 4)) return nullptr;
+        switch (stages) {
+        case 2: return persistent_fn_lanes<2, false, 4>(lanes);
+        case 3: return persistent_fn_lanes<3, false, 4>(lanes);
+        case 4: return persistent_fn_lanes<4, false, 4>(lanes);
         default: return nullptr;
         }
     }

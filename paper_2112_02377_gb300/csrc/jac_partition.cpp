@@ -176,6 +176,77 @@ Error make_plan(const HostCSR& A, jac_splitting s, int32_t nparts, const jac_opt
     return Error();
 }
 
+// Stopping on local convergence (Sec. 3, the parallel form of Algorithm 1):
+// the rows each partition tests.  Band splittings: band p holds its rows.
+// Substructuring: subdomain s holds the nodes of its box of grid cells; along
+// an axis the box t covers the closed node range [c_t, c_{t+1}] (c_0 = 0,
+// c_p = g - 1 at the grid's ends), so a node on cut plane c_t belongs to the
+// boxes t-1 and t, and an interface node to 2, 4 or 8 subdomains.
+Error local_row_sets(const Plan& plan, const jac_opts& o, std::vector<int32_t>& mem_ptr,
+                     std::vector<int32_t>& mem_part, std::vector<int32_t>& set_id)
+{
+    const int64_t n = (int64_t)plan.perm.size();
+    std::vector<int64_t> first(n + 1, 0);        // per new row: its sets (partition numbers)
+    std::vector<int64_t> parts;
+    parts.reserve(n + n / 8);
+    int64_t nparts = 0;
+    if (plan.splitting == JAC_BANDROW || plan.splitting == JAC_BANDROW_NNZ) {
+        nparts = plan.nparts();
+        for (int64_t p = 0; p < nparts; ++p)
+            for (int64_t r = plan.part_ptr[p]; r < plan.part_ptr[p + 1]; ++r) {
+                parts.push_back(p);
+                first[r + 1] = (int64_t)parts.size();
+            }
+    } else if (plan.splitting == JAC_SUBSTRUCT) {
+        const int64_t gx = o.grid[0], gy = o.grid[1], gz = o.grid[2];
+        const int64_t px = o.subdomains[0], py = o.subdomains[1], pz = o.subdomains[2];
+        nparts = px * py * pz;
+        // boxes of each coordinate along each axis (one, or two on a cut plane)
+        auto axis_boxes = [](int64_t g, int64_t p, std::vector<int64_t>& lo, std::vector<int64_t>& cnt) {
+            lo.assign(g, 0);
+            cnt.assign(g, 1);
+            for (int64_t v = 0; v < g; ++v) {
+                int64_t below = 0;
+                bool on = false;
+                axis_side(v, g, p, below, on);
+                lo[v] = below;                  // a cut c_t = v (t = below + 1) joins boxes below, below + 1
+                cnt[v] = on ? 2 : 1;
+            }
+        };
+        std::vector<int64_t> lx, ly, lz, cx, cy, cz;
+        axis_boxes(gx, px, lx, cx);
+        axis_boxes(gy, py, ly, cy);
+        axis_boxes(gz, pz, lz, cz);
+        for (int64_t r = 0; r < n; ++r) {
+            const int64_t i = plan.perm[r];
+            const int64_t node = o.node_of_row ? o.node_of_row[i] : i;
+            const int64_t X = node % gx, Y = (node / gx) % gy, Z = node / (gx * gy);
+            for (int64_t a = 0; a < cz[Z]; ++a)
+                for (int64_t bb = 0; bb < cy[Y]; ++bb)
+                    for (int64_t q = 0; q < cx[X]; ++q)
+                        parts.push_back((lx[X] + q) + px * ((ly[Y] + bb) + py * (lz[Z] + a)));
+            first[r + 1] = (int64_t)parts.size();
+        }
+    } else {
+        return Error(JAC_EINVAL, "local stopping needs a band or substructuring splitting");
+    }
+    if ((int64_t)parts.size() > INT32_MAX - 64) return Error(JAC_EINVAL, "too many local set entries");
+    // number the non-empty sets densely, in partition order
+    std::vector<int32_t> dense(nparts, -1);
+    for (int64_t p : parts) dense[p] = 0;
+    set_id.clear();
+    for (int64_t p = 0; p < nparts; ++p)
+        if (dense[p] == 0) {
+            dense[p] = (int32_t)set_id.size();
+            set_id.push_back((int32_t)p);
+        }
+    mem_ptr.resize(n + 1);
+    for (int64_t r = 0; r <= n; ++r) mem_ptr[r] = (int32_t)first[r];
+    mem_part.resize(parts.size());
+    for (size_t e = 0; e < parts.size(); ++e) mem_part[e] = dense[parts[e]];
+    return Error();
+}
+
 Error make_scaled_form(const HostCSR& A, const Plan& plan, ScaledForm& tf)
 {
     const int64_t n = A.n;

@@ -24,6 +24,7 @@ JAC_MEM_HOST, JAC_MEM_DEVICE = 0, 1
 JAC_FP64, JAC_MIXED = 0, 1
 JAC_NORM_REL2, JAC_NORM_INF = 2, 0
 JAC_SYNC_GRID, JAC_SYNC_NEIGHBOUR, JAC_SYNC_ASYNC = 0, 1, 2
+JAC_STOP_GLOBAL, JAC_STOP_LOCAL = 0, 1
 
 SPLITTINGS = {"bandrow": JAC_BANDROW, "bandrow_nnz": JAC_BANDROW_NNZ, "substruct": JAC_SUBSTRUCT}
 _STATUS_NAMES = ["JAC_OK", "JAC_EINVAL", "JAC_ENOMEM", "JAC_ECUDA", "JAC_ESINGULAR", "JAC_ENOTCONV",
@@ -63,7 +64,7 @@ class jac_opts(ctypes.Structure):
                 ("debug", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("history", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("timeout_cycles", ctypes.c_uint64),
-                ("fault_skip_cta", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("fault_skip_cta", ctypes.c_int32), ("device", ctypes.c_int32), ("stop", ctypes.c_int32)]
 
 
 class jac_stats_t(ctypes.Structure):
@@ -74,7 +75,9 @@ class jac_stats_t(ctypes.Structure):
                [(f, ctypes.c_double) for f in ("last_relres", "last_res2", "last_resinf", "last_ms",
                                                  "bytes_per_sweep_fp64", "bytes_per_sweep_fp32")] + \
                [(f, ctypes.c_int32) for f in ("variant", "precision", "splitting", "nrhs", "tile_rows",
-                                                "ctas_per_sm", "lanes_per_row", "sync", "stages")]
+                                                "ctas_per_sm", "lanes_per_row", "sync", "stages", "stop",
+                                                "stop_part")] + \
+               [("stop_local", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

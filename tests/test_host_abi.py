@@ -338,3 +338,29 @@ def test_noalloc_entry_point_checks_arguments_and_reports_a_missing_device():
     assert st == J.JAC_EINVAL and b"n must be" in L.jac_last_error(None)
     st = L.jac_sweep_noalloc(A.n, P(rp), P(cl), P(vl), P(b), P(x0), P(out), 1, ctypes.byref(rel), None)
     assert st == J.JAC_ECUDA and L.jac_last_error(None).startswith(b"jac_sweep_noalloc: ")
+
+
+def test_local_stop_options_are_checked_before_any_device_call():
+    """JAC_STOP_LOCAL needs FP64, the infinity norm, grid-synchronised sweeps
+    and the persistent kernel with 1, 2 or 4 lanes; batched and split
+    contexts keep the global test.  All rejected on the host."""
+    A = W.laplace7(6)
+    b = np.ones(A.n)
+    bad = [dict(norm=J.JAC_NORM_REL2), dict(norm=J.JAC_NORM_INF, precision=J.JAC_MIXED),
+           dict(norm=J.JAC_NORM_INF, sync=J.JAC_SYNC_NEIGHBOUR), dict(norm=J.JAC_NORM_INF, variant=1),
+           dict(norm=J.JAC_NORM_INF, variant=3), dict(norm=J.JAC_NORM_INF, tile_rows=224),
+           dict(norm=J.JAC_NORM_INF, lanes_per_row=8)]
+    for kw in bad:
+        with pytest.raises(J.JacobiError) as ei:
+            J.jac_setup(A, b, J.JAC_BANDROW, 2, J.opts(stop=J.JAC_STOP_LOCAL, **kw))
+        assert ei.value.status == J.JAC_EINVAL and "JAC_STOP_LOCAL" in str(ei.value), kw
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup(A, b, J.JAC_BANDROW, 2, J.opts(stop=2))
+    assert ei.value.status == J.JAC_EINVAL
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup_batched([A], [b], J.opts(stop=J.JAC_STOP_LOCAL, norm=J.JAC_NORM_INF))
+    assert ei.value.status == J.JAC_EINVAL
+    with pytest.raises(J.JacobiError) as ei:
+        J.jac_setup_local(A.n, W.cell_box_locals("laplace7", 6, (2, 1, 1)), b,
+                          J.opts(stop=J.JAC_STOP_LOCAL, norm=J.JAC_NORM_INF))
+    assert ei.value.status == J.JAC_EINVAL
