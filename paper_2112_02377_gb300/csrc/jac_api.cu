@@ -92,6 +92,13 @@ struct jac_ctx {
     int sms = 1;
     int ntiles = 0, emax = 0, rows_per_tile = 256, stages = 4, grid = 0, threads = 0, smem = 0;
     int lanes = 1;                        // lanes per row (persistent variant, 256 threads)
+    // stopping on local convergence (JAC_STOP_LOCAL)
+    int stop = JAC_STOP_GLOBAL;
+    int* d_mem_ptr = nullptr;             // rows+1: each row's local sets ...
+    int* d_mem_part = nullptr;            // ... as dense set numbers
+    unsigned long long* d_loc = nullptr;  // [3][nloc] per-set maxima of |r| (order keys)
+    int nloc = 0;
+    std::vector<int32_t> h_set_id;        // partition number of each dense set
     const void* pfn64 = nullptr;
     const void* pfnmix = nullptr;
     const void* pfnmix32 = nullptr;    // batched mixed: the FP32 sweeps of a cycle (pfnmix: its FP64 pass)
@@ -260,6 +267,8 @@ DevMat devmat(const jac_ctx* c)
     m.d = c->d_d;
     m.n_own = (int)(c->split ? c->n_own : c->n);
     m.slot_info = c->d_slot_info;
+    m.mem_ptr = c->d_mem_ptr;
+    m.mem_part = c->d_mem_part;
     return m;
 }
 
@@ -277,6 +286,8 @@ DevVec devvec(const jac_ctx* c)
     v.dec = c->d_part ? c->d_part + 2 * (size_t)c->nslots : nullptr;
     v.nslots = c->nslots;
     v.trace = c->d_trace;
+    v.loc = c->d_loc;
+    v.nloc = c->nloc;
     return v;
 }
 
@@ -506,6 +517,7 @@ jac_status arm(jac_ctx* c, int test, int mixed, long long k_limit, long long k_d
 {
     if (c->d_trace)
         CK(c, cudaMemsetAsync(c->d_trace, 0, 4 * sizeof(unsigned long long) * c->grid, stream_of(c)));
+    if (c->d_loc) CK(c, cudaMemsetAsync(c->d_loc, 0, 3 * sizeof(unsigned long long) * c->nloc, stream_of(c)));
     CK(c, launch_arm(c->d_ctl, test, mixed, c->o.inner_sweeps, k_limit, k_delta, tol, c->o.norm, c->d_hist, c->hist_cap,
                      (long long)c->o.timeout_cycles, c->o.fault_skip_cta, stream_of(c)));
     return JAC_OK;
@@ -533,6 +545,7 @@ void destroy(jac_ctx* c)
     dfree(c->d_dep_ptr); dfree(c->d_dep); dfree(c->d_done); dfree(c->d_e[0]); dfree(c->d_e[1]); dfree(c->d_dlt);
     dfree(c->d_part); dfree(c->d_ctl); dfree(c->d_hist); dfree(c->d_perm); dfree(c->d_stage); dfree(c->d_stage2);
     dfree(c->d_bmap); dfree(c->d_slot_info);
+    dfree(c->d_mem_ptr); dfree(c->d_mem_part); dfree(c->d_loc);
     dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0);
     dfree(c->d_row1); dfree(c->d_nnz1); dfree(c->d_cta0);
     dfree(c->d_blk0); dfree(c->d_blk); dfree(c->d_lcol); dfree(c->d_trace);
@@ -597,6 +610,16 @@ jac_status check_opts(const jac_opts& o, jac_ctx* err_ctx)
         return fail(err_ctx, JAC_EINVAL, "opts.stages must be 0, 2, 3 or 4");
     if (o.sync != JAC_SYNC_GRID && o.sync != JAC_SYNC_NEIGHBOUR && o.sync != JAC_SYNC_ASYNC)
         return fail(err_ctx, JAC_EINVAL, "opts.sync must be JAC_SYNC_GRID, JAC_SYNC_NEIGHBOUR or JAC_SYNC_ASYNC");
+    if (o.stop != JAC_STOP_GLOBAL && o.stop != JAC_STOP_LOCAL)
+        return fail(err_ctx, JAC_EINVAL, "opts.stop must be JAC_STOP_GLOBAL or JAC_STOP_LOCAL");
+    if (o.stop == JAC_STOP_LOCAL) {
+        if (o.precision != JAC_FP64 || o.norm != JAC_NORM_INF || o.sync != JAC_SYNC_GRID)
+            return fail(err_ctx, JAC_EINVAL, "JAC_STOP_LOCAL needs JAC_FP64, JAC_NORM_INF and JAC_SYNC_GRID");
+        if ((o.variant != 0 && o.variant != 2) || (o.tile_rows != 0 && o.tile_rows != 256) ||
+            o.lanes_per_row == 8)
+            return fail(err_ctx, JAC_EINVAL,
+                        "JAC_STOP_LOCAL runs in the persistent kernel with 256-thread tiles and 1, 2 or 4 lanes per row");
+    }
     return JAC_OK;
 }
 
@@ -620,21 +643,21 @@ double time_per_sweep(jac_ctx* c)
         const int64_t inner = std::max<int64_t>(2, c->o.inner_sweeps);
         const int64_t cyc = 2 * inner;
         jac_status st = jac_solve(c, 0.0, cyc - 1, &k, &rel);
-        if ((st == JAC_OK || st == JAC_ENOTCONV) && k > 0) warm = c->last_ms / (double)k;
+        if ((st == JAC_OK || st == JAC_ENOTCONV) && k > 0 && c->last_ms > 0.0) warm = c->last_ms / (double)k;
         const int64_t ncyc = std::min<int64_t>(
             64, std::max<int64_t>(2, (int64_t)std::ceil(kTargetMs / std::max(warm * inner, 1e-6))));
         for (int rep = 0; rep < 3; ++rep) {
             jac_set_x(c, nullptr, JAC_MEM_HOST);
             st = jac_solve(c, 0.0, ncyc * inner - 1, &k, &rel);
-            if ((st != JAC_OK && st != JAC_ENOTCONV) || k < ncyc * inner - 1) break;
+            if ((st != JAC_OK && st != JAC_ENOTCONV) || k < ncyc * inner - 1 || !(c->last_ms > 0.0)) break;
             t.push_back(c->last_ms / (double)k);
         }
     } else {
         double rel = 0.0;
-        if (jac_sweep(c, 8, &rel) == JAC_OK) warm = c->last_ms / 8.0;
+        if (jac_sweep(c, 8, &rel) == JAC_OK && c->last_ms > 0.0) warm = c->last_ms / 8.0;
         const int nsw = (int)std::min<double>(8192.0, std::max(32.0, std::ceil(kTargetMs / std::max(warm, 1e-6))));
         for (int rep = 0; rep < 3; ++rep) {
-            if (jac_sweep(c, nsw, &rel) != JAC_OK) break;
+            if (jac_sweep(c, nsw, &rel) != JAC_OK || !(c->last_ms > 0.0)) break;
             t.push_back(c->last_ms / (double)nsw);
         }
     }
@@ -790,6 +813,7 @@ void jac_opts_default(jac_opts* o)
     o->timeout_cycles = 0;
     o->fault_skip_cta = -1;
     o->device = -1;
+    o->stop = JAC_STOP_GLOBAL;
 }
 
 const char* jac_last_error(const jac_ctx* ctx)
@@ -881,6 +905,9 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
     c->interface_rows = plan.interface_rows;
     c->K = o.sweeps_per_graph;
     c->halo_entries = halo_entries;
+    c->stop = o.stop;
+    if (c->stop == JAC_STOP_LOCAL && (sp || o.nrhs != 1))
+        return fail(nullptr, JAC_EINVAL, "JAC_STOP_LOCAL is supported by jac_setup contexts only");
     jac_ctx* C = c.get();
     const int64_t rows = tf.n, nnz_off = c->nnz_off;
     if (rows > INT32_MAX - 64) return fail(nullptr, JAC_EINVAL, "n too large");
@@ -911,8 +938,10 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
     c->lanes = 1;
     if (c->variant == 2 && c->rows_per_tile == 256) {
         const double avg = rows > 0 ? (double)nnz_off_of(tf) / (double)rows : 0.0;
+        // local stopping is compiled for 1, 2 and 4 lanes
+        const int lane_cap = (o.stop == JAC_STOP_LOCAL) ? 4 : 8;
         if (o.lanes_per_row) c->lanes = o.lanes_per_row;
-        else while (c->lanes < 8 && avg / (2.0 * c->lanes) >= 8.0) c->lanes *= 2;
+        else while (c->lanes < lane_cap && avg / (2.0 * c->lanes) >= 8.0) c->lanes *= 2;
     } else if (o.lanes_per_row > 1) {
         return fail(nullptr, JAC_EINVAL, "opts.lanes_per_row > 1 needs variant 2 with 256-thread tiles");
     }
@@ -941,8 +970,9 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
         } else {
             c->sync = (c->variant == 2 && c->rows_per_tile == 256) ? o.sync : JAC_SYNC_GRID;
             c->ns = c->sync == JAC_SYNC_NEIGHBOUR;
-            // kernel form 3: the grid-synchronised FP64 kernel over a split interface layout
-            const int form = sp ? 3 : c->sync;
+            // kernel form 3: the grid-synchronised FP64 kernel over a split interface layout;
+            // form 4: the grid-synchronised FP64 kernel with the local stopping tests
+            const int form = sp ? 3 : c->stop == JAC_STOP_LOCAL ? 4 : c->sync;
             c->pfn64 = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, form);
             c->pfn64grid = persistent_kernel(c->rows_per_tile, c->stages, false, c->lanes, sp ? 3 : JAC_SYNC_GRID);
             // split layouts are FP64 only: no mixed kernels.  A mixed cycle runs as
@@ -1028,6 +1058,9 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
             c->sms = prop.multiProcessorCount;
         }
     }
+    if (c->stop == JAC_STOP_LOCAL && (c->variant != 2 || !c->pfn64))
+        return fail(nullptr, JAC_EINVAL,
+                    "JAC_STOP_LOCAL: the persistent kernel (256-thread tiles, 1, 2 or 4 lanes) cannot run here");
     if (c->variant == 1) {
         c->grid = (int)((n + 255) / 256);
         c->emax = 0;
@@ -1099,6 +1132,19 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
         CK(nullptr, dalloc(&c->d_dlt, n + 16));
     }
     CK(nullptr, dalloc(&c->d_part, 2 * (size_t)c->nslots + 4 + 2));
+    if (c->stop == JAC_STOP_LOCAL) {
+        std::vector<int32_t> mem_ptr, mem_part;
+        const Error el = local_row_sets(plan, o, mem_ptr, mem_part, c->h_set_id);
+        if (!el.ok()) return fail(nullptr, el.st, el.msg);
+        c->nloc = (int)c->h_set_id.size();
+        CK(nullptr, dalloc(&c->d_mem_ptr, mem_ptr.size()));
+        CK(nullptr, dalloc(&c->d_mem_part, mem_part.size() + 1));
+        CK(nullptr, dalloc(&c->d_loc, 3 * (size_t)c->nloc));
+        CK(nullptr, cudaMemcpy(c->d_mem_ptr, mem_ptr.data(), mem_ptr.size() * 4, cudaMemcpyHostToDevice));
+        if (!mem_part.empty())
+            CK(nullptr, cudaMemcpy(c->d_mem_part, mem_part.data(), mem_part.size() * 4, cudaMemcpyHostToDevice));
+        CK(nullptr, cudaMemset(c->d_loc, 0, 3 * sizeof(unsigned long long) * c->nloc));
+    }
     if (c->variant >= 2) CK(nullptr, dalloc(&c->d_trace, 4 * (size_t)c->grid));
     CK(nullptr, dalloc(&c->d_ctl, 1));
     CK(nullptr, dalloc(&c->d_perm, n));
@@ -1342,6 +1388,8 @@ try {
     if (o.variant || o.tile_rows || o.ctas_per_sm)
         return fail(nullptr, JAC_EINVAL, "autotune needs variant = tile_rows = ctas_per_sm = 0");
     const bool async = (o.sync == JAC_SYNC_ASYNC);
+    // local stopping runs in the grid-synchronised 256-thread geometry with 1, 2 or 4 lanes
+    const bool local_stop = (o.stop == JAC_STOP_LOCAL);
     // the automatic lane count (its own arithmetic: see jac_opts.lanes_per_row)
     int la = o.lanes_per_row;
     if (la == 0) {
@@ -1362,6 +1410,7 @@ try {
     if (la >= 2 && !async) cand.push_back({2, 256, 2, 0, JAC_SYNC_GRID, 2});
     else cand.push_back({2, 256, 3, 0});
     auto add = [&](const Geometry& g) {
+        if (local_stop && (g.variant != 2 || g.rows != 256 || g.sync != JAC_SYNC_GRID || g.lanes == 8)) return;
         for (const Geometry& h : cand)
             if (h.variant == g.variant && h.rows == g.rows && h.ctas == g.ctas && h.lanes == g.lanes &&
                 h.sync == g.sync && h.stages == g.stages)
@@ -1411,6 +1460,7 @@ try {
     jac_opts_default(&o);
     if (o_in) o = *o_in;
     if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
+    if (o.stop != JAC_STOP_GLOBAL) return fail(nullptr, JAC_EINVAL, "JAC_STOP_LOCAL is supported by jac_setup contexts only");
     jac_status st = check_opts(o, nullptr);
     if (st != JAC_OK) return st;
     if (o.precision != JAC_FP64 || o.nrhs != 1 || o.transpose || (o.variant != 0 && o.variant != 2) ||
@@ -1503,6 +1553,7 @@ try {
     jac_opts o;
     jac_opts_default(&o);
     if (o_in) o = *o_in;
+    if (o.stop != JAC_STOP_GLOBAL) return fail(nullptr, JAC_EINVAL, "JAC_STOP_LOCAL is supported by jac_setup contexts only");
     if (o.autotune) {
         if (o.tile_rows) return fail(nullptr, JAC_EINVAL, "autotune needs tile_rows = 0");
         jac_ctx* best = nullptr;
@@ -1813,7 +1864,7 @@ try {
     if (st != JAC_OK) return st;
     CK(c, s ? cudaStreamSynchronize(s) : cudaDeviceSynchronize());
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     c->last_ms = ms;
     const JacCtl& h = c->h_ctl[0];
     st = status_from_ctl(c, h);
@@ -1940,10 +1991,11 @@ static jac_status solve_impl(jac_ctx* c, double tol, int64_t maxit, int64_t* swe
         std::swap(ea, eb);
     }
     CK(c, cudaEventRecord(c->ev1, s));
-    cudaError_t e = cudaEventSynchronize(eb);
+    // ev1 follows eb on the stream: once it has completed, so has every step
+    cudaError_t e = cudaEventSynchronize(c->ev1);
     if (e != cudaSuccess) return cuda_fail(c, e, "solve loop");
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     c->last_ms = ms;
     // the later copy (hb) holds the final state; keep it in slot 0
     c->h_ctl[0] = *hb;
@@ -2122,6 +2174,10 @@ try {
     out->lanes_per_row = c->variant >= 2 ? c->lanes : 1;
     out->sync = c->sync;
     out->stages = c->variant >= 2 ? c->stages : 0;
+    out->stop = c->stop;
+    const int lp = c->h_ctl[0].loc_part;
+    out->stop_part = (c->stop == JAC_STOP_LOCAL && lp >= 0 && lp < (int)c->h_set_id.size()) ? c->h_set_id[lp] : -1;
+    out->stop_local = out->stop_part >= 0 ? c->h_ctl[0].loc_val : 0.0;
     out->ctas_per_sm = (c->variant >= 2 && c->n > 0 && c->grid > 0) ? c->grid / std::max(1, c->sms) : 0;
     return JAC_OK;
 } catch (...) {
