@@ -37,6 +37,10 @@ partitioned procedures"):
 * ``adjoint_gradients``   -- dL/db = lambda, dL/dA_ij = -lambda_i x_j with
   A^T lambda = dL/dx, the lambda solve done by the same Jacobi loop.
 
+``sweep_omp`` (``jacobi_omp.c``) is not part of the checker: it is the same
+row loop spread over the host's cores with OpenMP, timed by the benchmark as
+a multi-core CPU baseline.
+
 Parity pins for every function are in ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
@@ -68,6 +72,55 @@ def build(force: bool = False) -> str:
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
+
+
+_SRC_OMP = os.path.join(_HERE, "jacobi_omp.c")
+_SO_OMP = os.path.join(_BUILD, "libjacobi_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile the multi-core CPU baseline (OpenMP) with gcc."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO_OMP) or os.path.getmtime(_SO_OMP) < os.path.getmtime(_SRC_OMP):
+        tmp = _SO_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               "-o", tmp, _SRC_OMP, "-lm"])
+        os.replace(tmp, _SO_OMP)
+    return _SO_OMP
+
+
+def _omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            build_omp()
+            L = ctypes.CDLL(_SO_OMP)
+            P = ctypes.c_void_p
+            L.jo_sweep_omp.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, P, P, P]
+            L.jo_sweep_omp.restype = None
+            L.jo_omp_threads.restype = ctypes.c_int
+            _lib_omp = L
+    return _lib_omp
+
+
+def omp_threads() -> int:
+    """Threads the multi-core baseline uses."""
+    return int(_omp().jo_omp_threads())
+
+
+def sweep_omp(A, b: np.ndarray, x: np.ndarray):
+    """The multi-core CPU baseline's sweep (a timing baseline, not a checker):
+    returns (x_next, sumsq, maxabs) like ``sweep``."""
+    M = _mat(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(M.n)
+    ss = ctypes.c_double()
+    mx = ctypes.c_double()
+    _omp().jo_sweep_omp(M.n, _p(M.rowptr), _p(M.col), _p(M.val), _p(M.d), _p(M.dinv), _p(b), _p(x), _p(y),
+                        ctypes.byref(ss), ctypes.byref(mx))
+    return y, ss.value, mx.value
 
 
 def _c():
