@@ -347,14 +347,22 @@ def secondary_batched(J, W, stream, local, oracle=True) -> dict:
             worst = max(worst, float(np.max(np.linalg.norm(rr, axis=0) / np.linalg.norm(b_, axis=0))))
             off += A_.n
         swr = sw.reshape(len(mats), 4)
+        # Algorithmic bytes.  A system's matrix is read once per sweep while any
+        # of its right-hand sides iterates: FP64 12 (nnz - n) + 4 (n + 1), FP32
+        # 8 (nnz - n) + 4 (n + 1).  Each (row, right-hand side) moves per FP64
+        # sweep b, y in and y out (24 B); per FP32 inner sweep r, f in and f out
+        # (12 B); a mixed cycle of m sweeps is one FP64 pass and m - 1 FP32 sweeps.
+        mat64 = [12.0 * (A_.nnz - A_.n) + 4.0 * (A_.n + 1) for A_ in mats]
+        mat32 = [8.0 * (A_.nnz - A_.n) + 4.0 * (A_.n + 1) for A_ in mats]
         if prec == "fp64":
-            mat_b = sum(float(swr[i].max()) * (12.0 * (A_.nnz - A_.n) + 4.0 * (A_.n + 1) + 8.0 * A_.n)
-                        for i, A_ in enumerate(mats))
-            vec_b = sum(float(swr[i].sum()) * 16.0 * A_.n for i, A_ in enumerate(mats))
+            mat_b = sum(float(swr[i].max()) * mat64[i] for i in range(len(mats)))
+            vec_b = sum(float(swr[i].sum()) * 24.0 * A_.n for i, A_ in enumerate(mats))
         else:
-            mat_b = sum(float(swr[i].max()) * (8.0 * (A_.nnz - A_.n) + 4.0 * (A_.n + 1) + 4.0 * A_.n)
+            frac64 = 1.0 / 128.0
+            mat_b = sum(float(swr[i].max()) * (frac64 * mat64[i] + (1.0 - frac64) * mat32[i])
+                        for i in range(len(mats)))
+            vec_b = sum(float(swr[i].sum()) * (frac64 * 24.0 + (1.0 - frac64) * 12.0) * A_.n
                         for i, A_ in enumerate(mats))
-            vec_b = sum(float(swr[i].sum()) * 8.0 * A_.n for i, A_ in enumerate(mats))
         sec = stt["last_ms"] * 1e-3
         gbs_b = (mat_b + vec_b) / sec / 1e9
         # FP64 instructions: every (system, right-hand side) FP64 sweep (all of
@@ -372,8 +380,9 @@ def secondary_batched(J, W, stream, local, oracle=True) -> dict:
                      "frac_of_fp64_pipe": round(t_f64 / sec, 4), "bound": "fp64" if t_f64 > t_hbm else "hbm",
                      "frac_of_bound": round(max(t_f64, t_hbm) / sec, 4),
                      "tile_rows": stt["tile_rows"], "ctas_per_sm": stt["ctas_per_sm"]}
-    out["bytes_note"] = ("each system's matrix once per sweep while any of its right-hand sides iterates, "
-                         "vectors per right-hand side sweep (FP32 phases at FP32 bytes for mixed)")
+    out["bytes_note"] = ("each system's matrix once per sweep while any of its right-hand sides iterates; per "
+                         "(row, right-hand side) b, y in, y out (24 B) per FP64 sweep and r, f in, f out (12 B) per "
+                         "FP32 sweep; a mixed cycle of 128 sweeps is one FP64 pass and 127 FP32 sweeps")
     out["speedup_mixed_over_fp64"] = round(out["fp64"]["seconds"] / out["mixed"]["seconds"], 3)
     if oracle:
         from oracle import oracle as O

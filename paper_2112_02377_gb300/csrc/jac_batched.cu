@@ -39,25 +39,37 @@ __device__ __forceinline__ void mbar_arrive_b(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Gathered entries per row the FP32 launch copies ahead (a 7-point row has 6).
+constexpr int GMAXE = 6;
+
+// Shared memory of the FP32 launch's two gather buffers (4 right-hand sides).
+__host__ __device__ constexpr int batched_gather_bytes(int rows, int nrhs, int part)
+{
+    return (part == 2 && nrhs == 4) ? 2 * GMAXE * rows * 16 : 0;
+}
+
 struct BStageLayout {
     int o_val, o_col, o_rp, o_c, bytes;   // o_c: the tile's b, NRHS per row (FP64 phases)
 };
 
-__host__ __device__ inline BStageLayout bstage_layout(int rows, int emax, int nrhs)
+// fp32: the stages of the FP32-sweep launch of a mixed cycle (4-byte values,
+// no right-hand side)
+__host__ __device__ inline BStageLayout bstage_layout(int rows, int emax, int nrhs, bool fp32 = false)
 {
     auto up = [](int v) { return (v + 127) & ~127; };
     BStageLayout L;
     L.o_val = 128;
-    L.o_col = L.o_val + up((emax + 4) * 8);
+    L.o_col = L.o_val + up((emax + 4) * (fp32 ? 4 : 8));
     L.o_rp = L.o_col + up((emax + 8) * 4);
     L.o_c = L.o_rp + up((rows + 12) * 4);
-    L.bytes = L.o_c + up((rows + 4) * nrhs * 8);
+    L.bytes = L.o_c + (fp32 ? 0 : up((rows + 4) * nrhs * 8));
     return L;
 }
 
-int batched_smem_bytes(int rows, int emax, int nrhs, int stages)
+int batched_smem_bytes(int rows, int emax, int nrhs, int stages, bool fp32)
 {
-    return stages * bstage_layout(rows, emax, nrhs).bytes + 2 * stages * 8 + 64;
+    return stages * bstage_layout(rows, emax, nrhs, fp32).bytes + batched_gather_bytes(rows, nrhs, fp32 ? 2 : 0) +
+           2 * stages * 8 + 64;
 }
 
 template <int NRHS>
@@ -91,6 +103,49 @@ __device__ __forceinline__ void load_rhs(const float* p, float (&v)[NRHS])
     }
 }
 
+// 16-byte asynchronous copy global -> shared, cached in L2 only (the iterate
+// changes every sweep and L1 is not coherent), and its group operations.
+__device__ __forceinline__ void cp_async16_cg(void* dst_smem, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int NRHS>
+__device__ __forceinline__ void store_rhs(float* p, const float (&v)[NRHS])
+{
+    if constexpr (NRHS == 4) {
+        __stcg(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    } else if constexpr (NRHS == 2) {
+        __stcg(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+    } else {
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) __stcg(p + q, v[q]);
+    }
+}
+
+template <int NRHS>
+__device__ __forceinline__ void store_rhs(double* p, const double (&v)[NRHS])
+{
+    if constexpr (NRHS % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < NRHS; q += 2) __stcg(reinterpret_cast<double2*>(p) + q / 2, make_double2(v[q], v[q + 1]));
+    } else {
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) __stcg(p + q, v[q]);
+    }
+}
+
 // acc[q] += sum_k T_k x[col_k][q] for the row's entries in stored order.
 template <int NRHS, class Real, class LdT, class LdC>
 __device__ __forceinline__ void brow_dot(Real (&acc)[NRHS], int kb, int len, const Real* __restrict__ xs, LdT ldt,
@@ -121,15 +176,24 @@ __device__ __forceinline__ void brow_dot(Real (&acc)[NRHS], int kb, int len, con
 // PART: 0 = every phase of the launch's sweeps; for the mixed cycle, 1 = its
 // FP64 residual pass only, 2 = its FP32 inner sweeps only.  A mixed graph step
 // alternates a PART 1 and a PART 2 launch per cycle, so the FP32 sweeps run in
-// a kernel without the FP64 code and its registers.
+// a kernel without the FP64 code and its registers.  The FP32 sweeps are bound
+// by the latency of the iterate gathers (the iterates outgrow L2) and the
+// registers that hold them cap the loads in flight.  With 4 right-hand sides
+// (16-byte iterate rows) PART 2 therefore gathers through shared memory: each
+// thread starts the cp.async copies of its row's entries in tile i+1 before it
+// sums its row of tile i, twice the loads in flight at the same occupancy and
+// without registers held; its stages hold FP32 data only.
 template <int NRHS, int STAGES, bool MIXED, int NWM, int PART = 0>
-__global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBatch bt, JacCtl* ctl, int max_sweeps)
+__global__ void __maxnreg__(128)
+k_batched(DevMat m, DevVec v, DevTiles t, DevBatch bt, JacCtl* ctl, int max_sweeps)
 {
     static_assert(PART == 0 || MIXED, "the split cycle is for mixed solves");
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int CT = NWM * 32, NW = NWM, ROWS = CT;
-    const BStageLayout L = bstage_layout(ROWS, t.emax, NRHS);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes);
+    const BStageLayout L = bstage_layout(ROWS, t.emax, NRHS, PART == 2);
+    // the FP32 launch with 4 right-hand sides: two gather buffers after the stages
+    constexpr int GBYTES = batched_gather_bytes(ROWS, NRHS, PART);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes + GBYTES);
     uint64_t* empty = full + STAGES;
     __shared__ double s_wss[NW][NRHS];
     __shared__ unsigned long long s_wmx[NW][NRHS];
@@ -153,7 +217,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
         s_tol = c->tol;
         s_norm = c->norm_kind;
         // the stages and their barriers must fit the dynamic shared memory of the launch
-        const bool fits = (unsigned long long)STAGES * L.bytes + 2ull * STAGES * 8 <= dynamic_smem_bytes();
+        const bool fits = (unsigned long long)STAGES * L.bytes + GBYTES + 2ull * STAGES * 8 <= dynamic_smem_bytes();
         if (!fits) atomicOr(&ctl->status, ST_CONFIG);
         s_start = fits && (c->done == DONE_RUNNING) && (c->status == 0);
         s_stop = 0;
@@ -267,7 +331,7 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
     long long evals = s_evals, outer = s_outer;
     long long jc = 0;
     int nbar = 0;
-    const int my_pair0 = bt.cta_pair0[blockIdx.x];
+    const int my_pair0 = PART == 2 ? 0 : bt.cta_pair0[blockIdx.x];   // FP32 sweeps keep no norms
     for (int sw = 0; sw < ksw; ++sw) {
         const int ph = phase_of(MIXED, pos, inner);
         const bool norm_ph = (ph == PH_P64 || ph == PH_P64R);
@@ -358,6 +422,132 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
             }
             b_consumer_sync(CT);
         };
+        if constexpr (!F64 && PART == 2 && NRHS == 4) {
+            // FP32 inner sweeps with 4 right-hand sides (16-byte iterate rows):
+            // the gathers of tile i+1 are in flight, as cp.async copies into
+            // shared memory, while tile i is summed (see the kernel's comment).
+            // Thread t's gathered row u sits at slot u * ROWS + t of its buffer,
+            // so each thread reads only what it copied itself and lanes read
+            // consecutive 16-byte slots.  Rows longer than GMAXE entries gather
+            // the rest when they are summed.
+            float4* gbuf = reinterpret_cast<float4*>(smem + STAGES * L.bytes);
+            auto wait_stage = [&](long long j) -> bool {
+                uint64_t* bar = &full[(int)(j % STAGES)];
+                const unsigned par = (unsigned)((j / STAGES) & 1);
+                bool ok = mbar_try_wait(bar, par);
+                if (!ok && !s_fail) {
+                    const long long t0 = clock64();
+                    while (!(ok = mbar_try_wait(bar, par))) {
+                        if (s_fail) break;
+                        if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); s_fail = 1; break; }
+                    }
+                }
+                return ok;
+            };
+            struct Pend {
+                int sidx, r, kb, len, p0, mk;
+                bool act, in, over;
+                float4 dl;
+            };
+            // wait for tile i's stage and start its gathers into buffer (i & 1)
+            auto issue = [&](int i, Pend& P) {
+                const int ti = tb + i;
+                const long long j = jc + i;
+                P.sidx = (int)(j % STAGES);
+                P.act = false;
+                P.in = false;
+                P.len = 0;
+                const int sys = __ldg(bt.tile_sys + ti);
+                if (sys != cur) {
+                    cur = sys;
+                    msk = ld_volatile_i32(bt.mask + sys);
+                }
+                P.mk = msk;
+                if (wait_stage(j) && msk != ALL) {
+                    P.act = true;
+                    const unsigned char* st = smem + P.sidx * L.bytes;
+                    const int r0 = __ldg(t.row0 + ti), r1 = __ldg(t.row1 + ti);
+                    P.p0 = __ldg(t.nnz0 + ti);
+                    P.over = (__ldg(t.nnz1 + ti) - P.p0) > emax;
+                    const int* srp = reinterpret_cast<const int*>(st + L.o_rp) - (r0 & ~3);
+                    const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (P.p0 & ~3);
+                    P.r = r0 + tid;
+                    P.in = P.r < r1;
+                    P.kb = P.in ? srp[P.r] : 0;
+                    P.len = P.in ? srp[P.r + 1] - P.kb : 0;
+                    if (P.in) P.dl = __ldcg(reinterpret_cast<const float4*>(v.dlt) + P.r);
+                    if (!P.over) {
+                        float4* dst = gbuf + (size_t)(i & 1) * GMAXE * ROWS + tid;
+#pragma unroll
+                        for (int u = 0; u < GMAXE; ++u)
+                            if (u < P.len) cp_async16_cg(dst + u * ROWS, reinterpret_cast<const float4*>(es) + scol[P.kb + u]);
+                    }
+                }
+                cp_async_commit();
+            };
+            Pend c, nx;
+            if (nt > 0) issue(0, c);
+            for (int i = 0; i < nt; ++i) {
+                if (i + 1 < nt) {
+                    issue(i + 1, nx);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                if (c.act && c.in) {
+                    const unsigned char* st = smem + c.sidx * L.bytes;
+                    float acc[4] = {c.dl.x, c.dl.y, c.dl.z, c.dl.w};
+                    if (!c.over) {
+                        const float* sv = reinterpret_cast<const float*>(st + L.o_val) - (c.p0 & ~3);
+                        const int* scol = reinterpret_cast<const int*>(st + L.o_col) - (c.p0 & ~3);
+                        const float4* src = gbuf + (size_t)(i & 1) * GMAXE * ROWS + tid;
+#pragma unroll
+                        for (int u = 0; u < GMAXE; ++u) {
+                            if (u < c.len) {
+                                const float tv = sv[c.kb + u];
+                                const float4 xv = src[u * ROWS];
+                                acc[0] = __fmaf_rn(tv, xv.x, acc[0]);
+                                acc[1] = __fmaf_rn(tv, xv.y, acc[1]);
+                                acc[2] = __fmaf_rn(tv, xv.z, acc[2]);
+                                acc[3] = __fmaf_rn(tv, xv.w, acc[3]);
+                            }
+                        }
+                        for (int u = GMAXE; u < c.len; ++u) {   // the rest of a long row, in order
+                            const float tv = sv[c.kb + u];
+                            const float4 xv = __ldcg(reinterpret_cast<const float4*>(es) + scol[c.kb + u]);
+                            acc[0] = __fmaf_rn(tv, xv.x, acc[0]);
+                            acc[1] = __fmaf_rn(tv, xv.y, acc[1]);
+                            acc[2] = __fmaf_rn(tv, xv.z, acc[2]);
+                            acc[3] = __fmaf_rn(tv, xv.w, acc[3]);
+                        }
+                    } else {
+                        for (int u = 0; u < c.len; ++u) {       // a tile larger than a stage: from global memory
+                            const float tv = __ldg(m.S32 + c.kb + u);
+                            const float4 xv = __ldcg(reinterpret_cast<const float4*>(es) + __ldg(m.col + c.kb + u));
+                            acc[0] = __fmaf_rn(tv, xv.x, acc[0]);
+                            acc[1] = __fmaf_rn(tv, xv.y, acc[1]);
+                            acc[2] = __fmaf_rn(tv, xv.z, acc[2]);
+                            acc[3] = __fmaf_rn(tv, xv.w, acc[3]);
+                        }
+                    }
+                    if (ph == PH_P32) {
+                        store_rhs<4>(ed + (size_t)c.r * 4, acc);
+                    } else {
+                        // y += f; a stopped right-hand side keeps its iterate
+                        double y[4];
+                        load_rhs<4>(v.x[xb] + (size_t)c.r * 4, y);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (!(c.mk & (1 << q))) y[q] = __dadd_rn(y[q], (double)acc[q]);
+                        store_rhs<4>(v.x[xb] + (size_t)c.r * 4, y);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive_b(&empty[c.sidx]);
+                c = nx;
+            }
+            jc += nt;
+        } else {
         for (int i = 0; i < nt; ++i, ++jc) {
             const int ti = tb + i;
             const int sys = __ldg(bt.tile_sys + ti);
@@ -432,20 +622,23 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
                         brow_dot<NRHS>(acc, kb, len, es, [&](int e) { return __ldg(m.S32 + e); },
                                        [&](int e) { return __ldg(m.col + e); });
                     if (in) {
+                        if (ph == PH_P32) {
+                            store_rhs<NRHS>(ed + (size_t)r * NRHS, acc);
+                        } else {
+                            // y += f; a stopped right-hand side keeps its iterate
+                            double y[NRHS];
+                            load_rhs<NRHS>(v.x[xb] + (size_t)r * NRHS, y);
 #pragma unroll
-                        for (int q = 0; q < NRHS; ++q) {
-                            if (ph == PH_P32) {
-                                __stcg(ed + (size_t)r * NRHS + q, acc[q]);
-                            } else if (!(msk & (1 << q))) {
-                                double* px = v.x[xb] + (size_t)r * NRHS + q;
-                                __stcg(px, __dadd_rn(__ldcg(px), (double)acc[q]));
-                            }
+                            for (int q = 0; q < NRHS; ++q)
+                                if (!(msk & (1 << q))) y[q] = __dadd_rn(y[q], (double)acc[q]);
+                            store_rhs<NRHS>(v.x[xb] + (size_t)r * NRHS, y);
                         }
                     }
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive_b(&empty[sidx]);
+        }
         }
         if constexpr (F64) {
             if (cur >= 0 && msk != ALL) finish(cur);
@@ -502,7 +695,8 @@ __global__ void __maxnreg__(128) k_batched(DevMat m, DevVec v, DevTiles t, DevBa
 template <int NRHS, bool MIXED, int NWM, int PART = 0>
 static const void* batched_fn()
 {
-    return reinterpret_cast<const void*>(&k_batched<NRHS, 4, MIXED, NWM, PART>);
+    // the FP32-sweep launch: more, smaller stages of FP32 data
+    return reinterpret_cast<const void*>(&k_batched<NRHS, PART == 2 ? BATCHED_FP32_STAGES : 4, MIXED, NWM, PART>);
 }
 
 template <int NRHS, int NWM>
@@ -519,7 +713,9 @@ static const void* batched_fn_part(bool mixed, int part)
 // Geometries: 224-row tiles (7 math warps + producer, 2 CTAs/SM) or 96-row
 // tiles (3 + 1 warps, 4 CTAs/SM: finer tiles for small systems).  Both leave
 // 128 registers a thread (16 warps per SM).  part: 0 = FP64 solves; 1 / 2 =
-// the FP64 pass / the FP32 sweeps of a mixed refinement cycle.
+// the FP64 pass / the FP32 sweeps of a mixed refinement cycle (part 2:
+// BATCHED_FP32_STAGES stages of FP32 data; with 4 right-hand sides, gathers
+// through shared memory one tile ahead).
 const void* batched_kernel(int nrhs, bool mixed, int rows, int part)
 {
     if (rows == 224) {

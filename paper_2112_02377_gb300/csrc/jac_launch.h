@@ -36,7 +36,10 @@ cudaError_t launch_reset_iterate(JacCtl* ctl, cudaStream_t s);
 cudaError_t launch_reset_bar(JacCtl* ctl, cudaStream_t s);
 // part: 0 = FP64 solves; 1 / 2 = the FP64 pass / the FP32 sweeps of a mixed cycle
 const void* batched_kernel(int nrhs, bool mixed, int rows, int part);
-int batched_smem_bytes(int rows, int emax, int nrhs, int stages);
+// stages of the FP32-sweep launch of a batched mixed cycle (FP32 data only; with
+// its gather buffers they fit in the shared memory of the FP64 launch's four)
+constexpr int BATCHED_FP32_STAGES = 4;
+int batched_smem_bytes(int rows, int emax, int nrhs, int stages, bool fp32 = false);
 int batched_threads(int rows);
 cudaError_t launch_batched(const void* fn, int grid, int threads, int smem, const DevMat& m, const DevVec& v,
                            const DevTiles& t, const DevBatch& bt, JacCtl* ctl, int max_sweeps, cudaStream_t s);
