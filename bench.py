@@ -431,8 +431,8 @@ def secondary_replay(J, W, stream, local, oracle=True) -> dict:
             for col, split in (("JB", J.JAC_BANDROW), ("JBO", J.JAC_BANDROW_NNZ), ("JSS", J.JAC_SUBSTRUCT)):
                 res = {"paper": dict(zip(("iterations", "comm_seconds", "total_seconds"), pq[P][col]))}
                 for stop, key in ((J.JAC_STOP_GLOBAL, "global_test"), (J.JAC_STOP_LOCAL, "local_test")):
-                    oo = dict(norm=J.JAC_NORM_INF, sweeps_per_graph=64, stop=stop, stream=stream.cuda_stream,
-                              device=local)
+                    oo = dict(norm=J.JAC_NORM_INF, sweeps_per_graph=64, stop=stop, autotune=1,
+                              stream=stream.cuda_stream, device=local)
                     if split == J.JAC_SUBSTRUCT:
                         c = J.jac_setup(A, b, split, 0, J.opts(grid=(g, g, g), subdomains=sub, **oo))
                     else:

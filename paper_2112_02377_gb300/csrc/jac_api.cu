@@ -96,6 +96,7 @@ struct jac_ctx {
     int stop = JAC_STOP_GLOBAL;
     int* d_mem_ptr = nullptr;             // rows+1: each row's local sets ...
     int* d_mem_part = nullptr;            // ... as dense set numbers
+    int* d_mem_head = nullptr;            // rows: first set | (number of sets << 24)
     unsigned long long* d_loc = nullptr;  // [3][nloc] per-set maxima of |r| (order keys)
     int nloc = 0;
     std::vector<int32_t> h_set_id;        // partition number of each dense set
@@ -269,6 +270,7 @@ DevMat devmat(const jac_ctx* c)
     m.slot_info = c->d_slot_info;
     m.mem_ptr = c->d_mem_ptr;
     m.mem_part = c->d_mem_part;
+    m.mem_head = c->d_mem_head;
     return m;
 }
 
@@ -545,7 +547,7 @@ void destroy(jac_ctx* c)
     dfree(c->d_dep_ptr); dfree(c->d_dep); dfree(c->d_done); dfree(c->d_e[0]); dfree(c->d_e[1]); dfree(c->d_dlt);
     dfree(c->d_part); dfree(c->d_ctl); dfree(c->d_hist); dfree(c->d_perm); dfree(c->d_stage); dfree(c->d_stage2);
     dfree(c->d_bmap); dfree(c->d_slot_info);
-    dfree(c->d_mem_ptr); dfree(c->d_mem_part); dfree(c->d_loc);
+    dfree(c->d_mem_ptr); dfree(c->d_mem_part); dfree(c->d_mem_head); dfree(c->d_loc);
     dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0);
     dfree(c->d_row1); dfree(c->d_nnz1); dfree(c->d_cta0);
     dfree(c->d_blk0); dfree(c->d_blk); dfree(c->d_lcol); dfree(c->d_trace);
@@ -1133,12 +1135,15 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
     }
     CK(nullptr, dalloc(&c->d_part, 2 * (size_t)c->nslots + 4 + 2));
     if (c->stop == JAC_STOP_LOCAL) {
-        std::vector<int32_t> mem_ptr, mem_part;
-        const Error el = local_row_sets(plan, o, mem_ptr, mem_part, c->h_set_id);
+        std::vector<int32_t> mem_ptr, mem_part, mem_head;
+        const Error el = local_row_sets(plan, o, mem_ptr, mem_part, mem_head, c->h_set_id);
         if (!el.ok()) return fail(nullptr, el.st, el.msg);
         c->nloc = (int)c->h_set_id.size();
         CK(nullptr, dalloc(&c->d_mem_ptr, mem_ptr.size()));
-        CK(nullptr, dalloc(&c->d_mem_part, mem_part.size() + 1));
+        CK(nullptr, dalloc(&c->d_mem_part, mem_part.size() + 8));
+        CK(nullptr, dalloc(&c->d_mem_head, mem_head.size() + 1));
+        if (!mem_head.empty())
+            CK(nullptr, cudaMemcpy(c->d_mem_head, mem_head.data(), mem_head.size() * 4, cudaMemcpyHostToDevice));
         CK(nullptr, dalloc(&c->d_loc, 3 * (size_t)c->nloc));
         CK(nullptr, cudaMemcpy(c->d_mem_ptr, mem_ptr.data(), mem_ptr.size() * 4, cudaMemcpyHostToDevice));
         if (!mem_part.empty())

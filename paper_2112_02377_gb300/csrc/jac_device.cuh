@@ -90,6 +90,7 @@ struct DevMat {
     // .. mem_ptr[r+1])); NULL otherwise.
     const int* mem_ptr;
     const int* mem_part;
+    const int* mem_head;      // row: first set | (number of sets << 24), -1 = none
 };
 
 struct DevVec {
@@ -206,30 +207,47 @@ __device__ __forceinline__ unsigned long long accumulate_residual_key(double yne
 }
 
 // Stopping on local convergence, called by all 32 lanes of a warp: every
-// lane with a row (row >= 0) raises the maxima of the row sets holding it to
-// the row's key.  A warp whose rows all lie in one set and no other (the
-// common case) makes one atomic; otherwise each row makes one per set.  The
-// maxima are integer keys, so the result does not depend on the order.
+// lane with a row (row >= 0; head = its mem_head word, loaded early by the
+// caller) raises the maxima of the row sets holding it to the row's key.  A
+// warp whose rows all lie in one set and no other (the common case) makes
+// one atomic; otherwise the rows' sets are fetched together and, set by set,
+// the lanes naming the same set combine their keys (an exact 64-bit max from
+// two 32-bit reductions) before one of them makes the atomic.  The maxima
+// are integer keys, so the result does not depend on the order.
+constexpr int LOC_MAX_SETS = 8;   // sets holding one row (a box corner node: 8)
 __device__ __forceinline__ void local_sets_update(unsigned long long* slot, const int* mem_ptr, const int* mem_part,
-                                                  int row, unsigned long long key)
+                                                  int row, int head, unsigned long long key)
 {
-    const bool has = row >= 0;
-    int mb = 0, me = 0, p = -1;
-    if (has) {
-        mb = __ldg(mem_ptr + row);
-        me = __ldg(mem_ptr + row + 1);
-        p = me > mb ? __ldg(mem_part + mb) : -1;
-    }
+    const bool has = row >= 0 && head >= 0;
+    const int cnt = has ? (int)((unsigned)head >> 24) : 0;
+    const int p = has ? (head & 0xffffff) : -1;
     const unsigned act = __ballot_sync(0xffffffffu, has);
     if (!act) return;
     const int src = __ffs(act) - 1;
     const int p0 = __shfl_sync(0xffffffffu, p, src);
-    const bool uniform = __all_sync(0xffffffffu, !has || (me - mb == 1 && p == p0));
-    if (uniform && p0 >= 0) {
+    const bool uniform = __all_sync(0xffffffffu, !has || (cnt == 1 && p == p0));
+    if (uniform) {
         const unsigned long long wk = warp_max(has ? key : 0ull);
         if ((threadIdx.x & 31) == 0) atomicMax(slot + p0, wk);
-    } else if (has) {
-        for (int e = mb; e < me; ++e) atomicMax(slot + __ldg(mem_part + e), key);
+        return;
+    }
+    int ps[LOC_MAX_SETS];
+    const int mb = cnt > 1 ? __ldg(mem_ptr + row) : 0;
+#pragma unroll
+    for (int e = 0; e < LOC_MAX_SETS; ++e) ps[e] = e == 0 ? p : (e < cnt ? __ldg(mem_part + mb + e) : -1);
+    const int cmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
+    const unsigned hi0 = (unsigned)(key >> 32), lo0 = (unsigned)(key & 0xffffffffull);
+#pragma unroll
+    for (int e = 0; e < LOC_MAX_SETS; ++e) {
+        if (e >= cmax) break;
+        const int pe = e < cnt ? ps[e] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, pe);
+        const unsigned hi = e < cnt ? hi0 : 0u;
+        const unsigned mhi = __reduce_max_sync(peers, hi);
+        const unsigned lo = (e < cnt && hi == mhi) ? lo0 : 0u;
+        const unsigned mlo = __reduce_max_sync(peers, lo);
+        if (pe >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+            atomicMax(slot + pe, ((unsigned long long)mhi << 32) | mlo);
     }
 }
 

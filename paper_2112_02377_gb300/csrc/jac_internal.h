@@ -117,10 +117,10 @@ int32_t split_max_multiplicity(int64_t n, int32_t nsub, const jac_local* sub);
 HostCSR transpose_csr(const HostCSR& A);
 // Stopping on local convergence: the rows each partition holds, as a CSR
 // over the new rows (mem_part: dense set numbers 0..nsets-1 of the non-empty
-// sets; set_id[q]: the partition number of set q -- band, or subdomain
-// sx + px (sy + py sz)).
+// sets; mem_head[r]: row r's first set | (its number of sets << 24); set_id[q]:
+// the partition number of set q -- band, or subdomain sx + px (sy + py sz)).
 Error local_row_sets(const Plan& plan, const jac_opts& o, std::vector<int32_t>& mem_ptr,
-                     std::vector<int32_t>& mem_part, std::vector<int32_t>& set_id);
+                     std::vector<int32_t>& mem_part, std::vector<int32_t>& mem_head, std::vector<int32_t>& set_id);
 void make_windows(const ScaledForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w);
 
 }  // namespace jac

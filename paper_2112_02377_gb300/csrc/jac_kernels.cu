@@ -783,22 +783,23 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
             // tree, so the same bits), then stores y' and takes the residual: one
             // DADD and the residual's DADD and DFMA per 32 rows.
             [[maybe_unused]] double pr_acc = 0.0, pr_xi = 0.0;
-            [[maybe_unused]] int pr_r = 0;
+            [[maybe_unused]] int pr_r = 0, pr_head = -1;
             [[maybe_unused]] bool pr_in = false;
-            [[maybe_unused]] auto pair_finish = [&](double bacc, double bxi, int br, bool bin) {
+            [[maybe_unused]] auto pair_finish = [&](double bacc, double bxi, int br, bool bin, int bhead) {
                 const bool q0 = (tid & 1) == 0;
                 const double recv = __shfl_xor_sync(0xffffffffu, q0 ? bacc : pr_acc, 1);
                 const double y = q0 ? pr_acc + recv : bacc + recv;
                 const double xv = q0 ? pr_xi : bxi;
                 const int row = q0 ? pr_r : br;
                 const bool has = q0 ? pr_in : bin;
+                [[maybe_unused]] const int head = q0 ? pr_head : bhead;
                 [[maybe_unused]] unsigned long long key = 0;
                 if (has) {
                     __stcg(xd + row, y);
                     if constexpr (LOC) key = accumulate_residual_key(y, xv, ss, mx);
                     else accumulate_residual(y, xv, ss, mx);
                 }
-                if constexpr (LOC) local_sets_update(lslot, m.mem_ptr, m.mem_part, has ? row : -1, key);
+                if constexpr (LOC) local_sets_update(lslot, m.mem_ptr, m.mem_part, has ? row : -1, head, key);
             };
             for (int i = 0; i < nt; ++i, ++jc) {
                 const int sidx = (int)(jc % STAGES);
@@ -825,7 +826,11 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                         const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
                         // y_i of this tile's row, read by the lane that will own the row
                         const bool odd = (i & 1) != 0;
-                        const double xt = (in && q == (odd ? 1 : 0)) ? __ldcg(xs + r) : 0.0;
+                        const bool owner = in && q == (odd ? 1 : 0);
+                        const double xt = owner ? __ldcg(xs + r) : 0.0;
+                        // the row's set word, fetched while the row is summed
+                        [[maybe_unused]] int hd = -1;
+                        if constexpr (LOC) hd = owner ? __ldg(m.mem_head + r) : -1;
                         double acc = lead ? sc[r] : 0.0;
                         if (!over)
                             acc = lanes_dot<LPR>(acc, kb, len, q, [&](int e) { return sv[e]; },
@@ -837,14 +842,18 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                             pr_xi = xt;
                             pr_r = r;
                             pr_in = in;
-                            if (i + 1 == nt) pair_finish(0.0, 0.0, 0, false);   // a last tile without a partner
+                            pr_head = hd;
+                            if (i + 1 == nt) pair_finish(0.0, 0.0, 0, false, -1);   // a last tile without a partner
                         } else {
-                            pair_finish(acc, xt, r, in);
+                            pair_finish(acc, xt, r, in, hd);
                         }
                     } else if (norm_ph) {
                         const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
                         const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
                         const double xi = (lead && own) ? __ldcg(xs + r) : 0.0;
+                        // the row's set word, fetched while the row is summed
+                        [[maybe_unused]] int hd = -1;
+                        if constexpr (LOC) hd = (lead && own) ? __ldg(m.mem_head + r) : -1;
                         double acc = lead ? sc[r] : 0.0;
                         if (!over)
                             acc = lanes_dot<LPR>(acc, kb, len, q, [&](int e) { return sv[e]; },
@@ -864,7 +873,8 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                             if constexpr (LOC) lkey = accumulate_residual_key(acc, xi, ss, mx);
                             else accumulate_residual(acc, xi, ss, mx);
                         }
-                        if constexpr (LOC) local_sets_update(lslot, m.mem_ptr, m.mem_part, (lead && own) ? r : -1, lkey);
+                        if constexpr (LOC)
+                            local_sets_update(lslot, m.mem_ptr, m.mem_part, (lead && own) ? r : -1, hd, lkey);
                         if constexpr (SPLIT) {
                             if (r0 >= m.n_own) {          // a tile of slot rows (tiles never mix the two)
                                 const unsigned info = lead ? __ldg(m.slot_info + (r - m.n_own)) : 0u;

@@ -183,7 +183,7 @@ Error make_plan(const HostCSR& A, jac_splitting s, int32_t nparts, const jac_opt
 // c_p = g - 1 at the grid's ends), so a node on cut plane c_t belongs to the
 // boxes t-1 and t, and an interface node to 2, 4 or 8 subdomains.
 Error local_row_sets(const Plan& plan, const jac_opts& o, std::vector<int32_t>& mem_ptr,
-                     std::vector<int32_t>& mem_part, std::vector<int32_t>& set_id)
+                     std::vector<int32_t>& mem_part, std::vector<int32_t>& mem_head, std::vector<int32_t>& set_id)
 {
     const int64_t n = (int64_t)plan.perm.size();
     std::vector<int64_t> first(n + 1, 0);        // per new row: its sets (partition numbers)
@@ -240,10 +240,17 @@ Error local_row_sets(const Plan& plan, const jac_opts& o, std::vector<int32_t>& 
             dense[p] = (int32_t)set_id.size();
             set_id.push_back((int32_t)p);
         }
+    if (set_id.size() >= ((size_t)1 << 24)) return Error(JAC_EINVAL, "local stopping: more than 2^24 partitions");
     mem_ptr.resize(n + 1);
     for (int64_t r = 0; r <= n; ++r) mem_ptr[r] = (int32_t)first[r];
     mem_part.resize(parts.size());
     for (size_t e = 0; e < parts.size(); ++e) mem_part[e] = dense[parts[e]];
+    // per row: its first set (low 24 bits) and its number of sets (high 8 bits)
+    mem_head.resize(n);
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t cnt = first[r + 1] - first[r];
+        mem_head[r] = cnt > 0 ? (int32_t)(((uint32_t)cnt << 24) | (uint32_t)dense[parts[first[r]]]) : -1;
+    }
     return Error();
 }
 

@@ -105,6 +105,25 @@ def test_paper_replay_local_stop_matches_the_oracle(q1_33, form, P, sub):
     assert abs(rel - np.max(np.abs(b - A.scipy() @ x))) <= vtol
 
 
+@pytest.mark.parametrize("form,P,sub", [("JSS", 64, (4, 4, 4)), ("JBO", 8, None)])
+def test_paper_replay_65cubed_local_stop_matches_the_oracle(form, P, sub):
+    """The Q1 65^3-node replay (the paper's cube-274625 table, ||r||_inf <
+    1e-8) with the local test: stopping sweep and partition as the oracle's."""
+    A, b = W.q1_laplace(65)
+    sets = _sets(A, form, P, sub)
+    xo, ko, po, loco, sto = O.solve_local(A, b, sets, tol=1e-8, maxit=20000)
+    assert sto == O.JO_OK
+    ctx = _setup(A, b, form, P, sub)
+    try:
+        k, rel, st = J.jac_solve(ctx, 1e-8, 20000)
+        stt = J.jac_stats(ctx)
+        x = J.jac_get_x(ctx)
+    finally:
+        J.jac_free(ctx)
+    assert st == J.JAC_OK and k == ko and stt["stop_part"] == po
+    assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
 @pytest.mark.parametrize("lanes,cps,stages", [(1, 2, 0), (1, 3, 0), (2, 2, 2), (2, 2, 3), (4, 2, 0)])
 def test_local_stop_every_geometry_stops_at_the_same_sweep(q1_33, lanes, cps, stages):
     """Each lane count, CTA count and stage count of the local-stop kernel
