@@ -156,11 +156,14 @@ typedef struct {
     int32_t debug;             /* 1: canary bytes in the 16-element padding after every device vector of
                                   jac_setup contexts, checked after each jac_sweep / jac_solve; a
                                   write past the end of a vector returns JAC_ECUDA */
-    int32_t autotune;          /* 1: jac_setup / jac_setup_batched time a few sweeps of every kernel
-                                  geometry (variant, tile_rows, ctas_per_sm) and keep the fastest;
-                                  jac_setup then re-cuts the CTA row ranges from the measured per-CTA
-                                  compute times while that shortens the sweep.  Needs
-                                  variant = tile_rows = ctas_per_sm = 0 */
+    int32_t autotune;          /* 1: jac_setup / jac_setup_batched time every kernel geometry
+                                  (variant, tile_rows, ctas_per_sm, lanes, stages, sync): the median
+                                  of three timings of about 2 ms or more each; the cost model's prior
+                                  geometry is kept unless another is more than 5 % faster.  jac_setup
+                                  then re-cuts the CTA row ranges from the measured per-CTA compute
+                                  times while that shortens the sweep.  Needs
+                                  variant = tile_rows = ctas_per_sm = 0.  With JAC_AUTOTUNE_LOG=1 in
+                                  the environment each candidate's time is printed on stderr. */
     int32_t history;           /* >0: record the relres of every evaluated iterate,
                                   up to this many entries (jac_get_history) */
     void* stream;              /* cudaStream_t for all work; NULL = legacy default stream */
