@@ -72,39 +72,53 @@ int batched_smem_bytes(int rows, int emax, int nrhs, int stages, bool fp32)
            2 * stages * 8 + 64;
 }
 
-template <int NRHS>
+// Loads of a row's NRHS values.  L1 = false: L2 only (ld.global.cg).  L1 =
+// true, for the iterate gathers of a sweep: cached in L1 too (ld.global.ca).
+// A sweep reads an iterate buffer that nobody writes during the sweep, after
+// the grid barrier whose release/acquire pair (atomic arrive, ld.acquire.gpu
+// and fences by each CTA's thread 0, then a CTA barrier) makes the previous
+// sweep's stores visible to these weak loads under the PTX memory model.
+template <bool L1, class T>
+__device__ __forceinline__ T ld_b(const T* p)
+{
+    if constexpr (L1) return __ldca(p);
+    else return __ldcg(p);
+}
+
+template <int NRHS, bool L1 = false>
 __device__ __forceinline__ void load_rhs(const double* p, double (&v)[NRHS])
 {
     if constexpr (NRHS % 2 == 0) {
 #pragma unroll
         for (int q = 0; q < NRHS; q += 2) {
-            const double2 t = __ldcg(reinterpret_cast<const double2*>(p) + q / 2);
+            const double2 t = ld_b<L1>(reinterpret_cast<const double2*>(p) + q / 2);
             v[q] = t.x;
             v[q + 1] = t.y;
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < NRHS; ++q) v[q] = __ldcg(p + q);
+        for (int q = 0; q < NRHS; ++q) v[q] = ld_b<L1>(p + q);
     }
 }
 
-template <int NRHS>
+template <int NRHS, bool L1 = false>
 __device__ __forceinline__ void load_rhs(const float* p, float (&v)[NRHS])
 {
     if constexpr (NRHS == 4) {
-        const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+        const float4 t = ld_b<L1>(reinterpret_cast<const float4*>(p));
         v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     } else if constexpr (NRHS == 2) {
-        const float2 t = __ldcg(reinterpret_cast<const float2*>(p));
+        const float2 t = ld_b<L1>(reinterpret_cast<const float2*>(p));
         v[0] = t.x; v[1] = t.y;
     } else {
 #pragma unroll
-        for (int q = 0; q < NRHS; ++q) v[q] = __ldcg(p + q);
+        for (int q = 0; q < NRHS; ++q) v[q] = ld_b<L1>(p + q);
     }
 }
 
-// 16-byte asynchronous copy global -> shared, cached in L2 only (the iterate
-// changes every sweep and L1 is not coherent), and its group operations.
+// 16-byte asynchronous copy global -> shared, cached in L2 only, and its group
+// operations.  (Through L1 as well, cp.async.ca, the FP32 sweeps of a mixed
+// batched solve took 8 % longer: the gathers land in shared memory anyway.)
 __device__ __forceinline__ void cp_async16_cg(void* dst_smem, const void* src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
@@ -157,7 +171,7 @@ __device__ __forceinline__ void brow_dot(Real (&acc)[NRHS], int kb, int len, con
         Real xv[BCHUNK][NRHS];
 #pragma unroll
         for (int u = 0; u < BCHUNK; ++u)
-            if (o + u < len) load_rhs<NRHS>(xs + (size_t)ldc(kb + o + u) * NRHS, xv[u]);
+            if (o + u < len) load_rhs<NRHS, true>(xs + (size_t)ldc(kb + o + u) * NRHS, xv[u]);
 #pragma unroll
         for (int u = 0; u < BCHUNK; ++u) {
             if (o + u >= lmax) break;

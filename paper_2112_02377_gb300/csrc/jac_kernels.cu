@@ -21,6 +21,22 @@ namespace jac {
 
 constexpr int CHUNK = 8;   // off-diagonal entries whose x loads are issued together
 
+// Load of an iterate entry.  L1 = true: cached in L1 as well (ld.global.ca).
+// Only for sweeps that read a buffer nobody writes during the sweep and that
+// start after the grid barrier: its release/acquire pair (atomic arrive,
+// ld.acquire.gpu and fences by each CTA's thread 0, then a CTA barrier) makes
+// the previous sweep's stores visible to these weak loads under the PTX
+// memory model, so no L1 line of an older sweep can be returned.  Rows of a
+// tile share most of their neighbours' lines (the row's own line, the lines
+// one grid line away that the previous tile loaded), which then come from L1
+// instead of L2.  Otherwise the load goes to L2 only (ld.global.cg).
+template <bool L1, class T>
+__device__ __forceinline__ T ld_iter(const T* p)
+{
+    if constexpr (L1) return __ldca(p);
+    else return __ldcg(p);
+}
+
 // ------------------------------------------------------------ row math -----
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -425,6 +441,8 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     // are paired, so that the add of a row's two chains and its residual serve
     // 32 rows per warp instruction instead of 16 (see pair_finish).
     constexpr bool PAIR2 = (LPR == 2 && !PIPE && !SPLIT && !MIXED && (SYNC == 0 || SYNC == 4));
+    // gathers of the iterate through L1 (see ld_iter): sweeps under the grid barrier
+    constexpr bool GL1 = (SYNC == 0 || SYNC == 3 || SYNC == 4);
     const StageLayout L = stage_layout(ROWS, t.emax);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * L.bytes);
     uint64_t* empty = full + STAGES;
@@ -827,14 +845,14 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                         // y_i of this tile's row, read by the lane that will own the row
                         const bool odd = (i & 1) != 0;
                         const bool owner = in && q == (odd ? 1 : 0);
-                        const double xt = owner ? __ldcg(xs + r) : 0.0;
+                        const double xt = owner ? ld_iter<GL1>(xs + r) : 0.0;
                         // the row's set word, fetched while the row is summed
                         [[maybe_unused]] int hd = -1;
                         if constexpr (LOC) hd = owner ? __ldg(m.mem_head + r) : -1;
                         double acc = lead ? sc[r] : 0.0;
                         if (!over)
                             acc = lanes_dot<LPR>(acc, kb, len, q, [&](int e) { return sv[e]; },
-                                                 [&](int e) { return __ldcg(xs + scol[e]); });
+                                                 [&](int e) { return ld_iter<GL1>(xs + scol[e]); });
                         else if (in)
                             acc = lanes_global<LPR>(m.S64, m.col, xs, kb, len, q, acc);
                         if (!odd) {
@@ -850,14 +868,14 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                     } else if (norm_ph) {
                         const double* sv = reinterpret_cast<const double*>(st + L.o_val) - (p0 & ~1);
                         const double* sc = reinterpret_cast<const double*>(st + L.o_c) - (r0 & ~1);
-                        const double xi = (lead && own) ? __ldcg(xs + r) : 0.0;
+                        const double xi = (lead && own) ? ld_iter<GL1>(xs + r) : 0.0;
                         // the row's set word, fetched while the row is summed
                         [[maybe_unused]] int hd = -1;
                         if constexpr (LOC) hd = (lead && own) ? __ldg(m.mem_head + r) : -1;
                         double acc = lead ? sc[r] : 0.0;
                         if (!over)
                             acc = lanes_dot<LPR>(acc, kb, len, q, [&](int e) { return sv[e]; },
-                                                 [&](int e) { return __ldcg(xs + scol[e]); });
+                                                 [&](int e) { return ld_iter<GL1>(xs + scol[e]); });
                         else if (in)
                             acc = lanes_global<LPR>(m.S64, m.col, xs, kb, len, q, acc);
                         acc = group_sum<LPR>(acc);
@@ -887,7 +905,7 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                         float acc = lead ? __ldcg(v.dlt + r) : 0.f;
                         if (!over)
                             acc = lanes_dot<LPR>(acc, kb, len, q, [&](int e) { return sv[e]; },
-                                                 [&](int e) { return __ldcg(es + scol[e]); });
+                                                 [&](int e) { return ld_iter<GL1>(es + scol[e]); });
                         else if (in)
                             acc = lanes_global<LPR>(m.S32, m.col, es, kb, len, q, acc);
                         acc = group_sum<LPR>(acc);
