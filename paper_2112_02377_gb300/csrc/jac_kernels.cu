@@ -348,7 +348,9 @@ __global__ void __launch_bounds__(256) k_row_sweep(DevMat m, DevVec v, JacCtl* c
 // for the next sweep is in flight while the grid waits at the barrier.
 // Consumer warps progress independently between sweep boundaries, which
 // overlaps one warp's L2 gathers of x with another warp's FP64 arithmetic.
-// x is gathered with ld.global.cg (it changes every sweep; L1 is not coherent).
+// Sweeps under the grid barrier gather x through L1 (ld_iter<true>: the
+// barrier's acquire orders every read after the stores of the sweep before);
+// the other forms gather with ld.global.cg.
 // After each sweep the CTAs publish partial norms, pass a bounded grid barrier
 // and each reduces all partials in the same fixed order, so every CTA takes
 // the same convergence decision.
@@ -358,11 +360,15 @@ struct StageLayout {
     int o_val, o_col, o_rp, o_c, bytes;   // o_c: the tile's b (FP64 phases)
 };
 
+// Regions start on 16-byte boundaries (what cp.async.bulk needs), not on
+// 128-byte lines: with 256-row tiles of 7-point rows three CTAs' stages then
+// fit the 196 KB shared-memory configuration instead of 228 KB, which leaves
+// the SM 60 KB of L1 for the iterate gathers instead of 28 KB.
 __host__ __device__ inline StageLayout stage_layout(int rows, int emax)
 {
-    auto up = [](int v) { return (v + 127) & ~127; };
+    auto up = [](int v) { return (v + 15) & ~15; };
     StageLayout L;
-    L.o_val = 128;                                  // 16-byte header (r0, r1, p0, p1) in the first line
+    L.o_val = 16;                                   // 16-byte header (r0, r1, p0, p1)
     L.o_col = L.o_val + up((emax + 4) * 8);
     L.o_rp = L.o_col + up((emax + 8) * 4);
     L.o_c = L.o_rp + up((rows + 12) * 4);
