@@ -665,7 +665,7 @@ k_batched(DevMat m, DevVec v, DevTiles t, DevBatch bt, JacCtl* ctl, int max_swee
         // ---- grid barrier
         b_consumer_sync(CT);
         if (tid == 0) {
-            __threadfence();
+            fence_acq_rel_gpu();       // release half of the barrier (see k_persistent)
             atomicAdd(&ctl->bar, 1ull);
             const unsigned long long target = (unsigned long long)(nbar + 1) * gridDim.x;
             const long long t0 = clock64();
@@ -674,7 +674,6 @@ k_batched(DevMat m, DevVec v, DevTiles t, DevBatch bt, JacCtl* ctl, int max_swee
                 if (clock64() - t0 > budget) { atomicOr(&ctl->status, ST_TIMEOUT); s_fail = 1; break; }
                 __nanosleep(32);
             }
-            __threadfence();
             s_stop_all = (int)(*(volatile unsigned*)bt.ndone >= (unsigned)bt.nsys);
         }
         ++nbar;

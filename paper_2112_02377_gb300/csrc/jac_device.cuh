@@ -379,6 +379,13 @@ __device__ __forceinline__ uint64_t policy_evict_first()
     return p;
 }
 
+// Release/acquire fence at GPU scope: with a relaxed atomic after it, the
+// release half of a grid barrier (lighter than __threadfence's fence.sc).
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
 {
     unsigned long long v;

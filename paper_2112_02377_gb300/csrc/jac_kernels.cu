@@ -1025,7 +1025,10 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                 __stcg(&slot->ss, b);
                 __stcg(&slot->mx, bm);
             }
-            __threadfence();
+            // release: this CTA's stores (ordered before by the CTA barrier) and
+            // its partial sums; acquire: the polling load that sees the last
+            // arrival, which the CTA barrier below extends to every thread
+            fence_acq_rel_gpu();
             if (!(s_skip == (int)blockIdx.x)) atomicAdd(&ctl->bar, 1ull);
             const unsigned long long target = (unsigned long long)(nbar + 1) * gridDim.x;
             const long long t0 = clock64();
@@ -1039,7 +1042,6 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                 tr_wait += tc_ - tr_mark;
                 tr_mark = tc_;
             }
-            __threadfence();
         }
         ++nbar;
         consumer_sync<CT>();
