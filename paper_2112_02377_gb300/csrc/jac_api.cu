@@ -1067,6 +1067,16 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
         c->grid = (int)((n + 255) / 256);
         c->emax = 0;
     }
+    // a split interface layout without calibrated costs: slot rows get their own estimate
+    std::vector<double> split_cost;
+    if (sp && !row_cost) {
+        split_cost.resize(rows);
+        for (int64_t r = 0; r < rows; ++r) {
+            const int64_t len = tf.rowptr[r + 1] - tf.rowptr[r];
+            split_cost[r] = r < sp->n_own ? default_row_cost(len) : slot_row_cost(len);
+        }
+        row_cost = &split_cost;
+    }
     if (c->variant == 2)
         make_tiling(tf, plan, c->rows_per_tile / c->lanes, c->emax, c->grid, tl, row_cost,
                     sp ? sp->n_own : INT64_MAX, sp ? sp->warp_rows : 1);

@@ -106,6 +106,8 @@ void dependency_lists(const HostCSR& A, const Plan& plan, std::vector<int64_t>& 
                       std::vector<int32_t>& recv_from, std::vector<int64_t>& recv);
 // row_cost: per-row cost estimates in the new order (NULL: default_row_cost).
 double default_row_cost(int64_t off_entries);
+// Cost estimate of a slot row (split interface block), same units.
+double slot_row_cost(int64_t entries);
 // Rows at and after align_from are cut only at align_from + multiples of align.
 void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
                  int64_t ctas, Tiling& t, const std::vector<double>* row_cost = nullptr,

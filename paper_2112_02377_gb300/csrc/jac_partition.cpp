@@ -333,6 +333,16 @@ double default_row_cost(int64_t off_entries)
     return 6.0 + (double)off_entries;
 }
 
+double slot_row_cost(int64_t entries)
+{
+    // A slot row of a split interface block carries a row's fixed cost twice:
+    // its own (row length, b slot, loop set-up) and its share of the in-warp
+    // assembly (shuffles and adds in subdomain order, the group's store and
+    // residual).  Per-CTA times of the 160^3 4x4x4 split sweep put a slot row
+    // of 2 to 5 entries at about 1.3 seven-point rows.
+    return 12.0 + (double)entries;
+}
+
 void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
                  int64_t ctas, Tiling& t, const std::vector<double>* row_cost, int64_t align_from, int32_t align)
 {
