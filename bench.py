@@ -528,7 +528,7 @@ def run_extra(args, local, stream):
     # the persistent kernel with each tile's x halo staged in shared memory
     A = W.laplace7(160)
     b = W.solution_and_rhs(A, 0)[1]
-    for variant, name in ((1, "one_launch_per_sweep"), (2, "persistent_l2_gather"), (3, "persistent_staged_halo")):
+    for variant, name in ((1, "one_launch_per_sweep"), (2, "persistent_cached_gather"), (3, "persistent_staged_halo")):
         c = J.jac_setup(A, b, J.JAC_BANDROW, 64, J.opts(variant=variant, sweeps_per_graph=250,
                                                          stream=stream.cuda_stream, device=local))
         J.jac_sweep(c, 250)

@@ -138,7 +138,7 @@ typedef struct {
     int32_t transpose;         /* 1 = solve with A^T instead of A (adjoint solves) */
     int32_t variant;           /* 0 = auto (2); 1 = one launch per sweep (row kernel);
                                   2 = persistent grid-synchronised pipelined kernel, x gathered
-                                  from L2; 3 = as 2 with each tile's x halo (its dependency list,
+                                  through L1/L2; 3 = as 2 with each tile's x halo (its dependency list,
                                   Sec. 4.2.2) staged into shared memory */
     int32_t tile_rows;         /* threads of a tile (one row each when lanes_per_row = 1): 0 = auto
                                   (256), 224, 256 or 480 (variant 2); 256 (variant 3) */
