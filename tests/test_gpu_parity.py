@@ -155,6 +155,11 @@ def test_lanes_per_row_auto_choice_and_mixed():
 
 @pytest.mark.parametrize("name,A,b", list(_cases())[:2])
 def test_variants_and_graph_batching_are_bit_identical(name, A, b):
+    """Every kernel form and every number of sweeps per launch gives the same
+    iterate bit for bit.  This also pins the persistent kernel's L1 gathers:
+    a launch of many sweeps reads, through L1, rows other CTAs wrote in the
+    sweep before, and must equal one launch per sweep and the row kernel
+    (a stale L1 line of an older sweep would change the iterate)."""
     outs = []
     for variant, K, rows, cps in [(1, 64, 256, 0), (2, 64, 256, 0), (2, 7, 256, 0), (2, 1, 256, 0),
                                   (2, 64, 256, 3), (2, 64, 480, 0), (2, 5, 480, 0), (2, 64, 224, 0),
