@@ -67,6 +67,7 @@ struct jac_ctx {
     int nslots = 0;
     unsigned long long* d_trace = nullptr;
     std::vector<int32_t> h_cta_row0;      // ctas+1: first row of each CTA (persistent variants)
+    std::vector<int32_t> h_cta_row1;      // ctas+1: first row of each CTA's second range (split layouts)
     std::vector<double> h_row_cost;       // per-row cost estimates the CTA ranges were cut with
     JacCtl* d_ctl = nullptr;
     JacCtl* h_ctl = nullptr;     // pinned mirrors [2]
@@ -84,6 +85,7 @@ struct jac_ctx {
     int* d_row1 = nullptr;         // batched: tile end rows / entries (tiles of active systems only)
     int* d_nnz1 = nullptr;
     int* d_cta0 = nullptr;
+    int* d_cta1 = nullptr;         // split layouts: each CTA's range of slot tiles
     int* d_blk0 = nullptr;
     int* d_blk = nullptr;
     int* d_lcol = nullptr;
@@ -301,6 +303,7 @@ DevTiles devtiles(const jac_ctx* c)
     t.row1 = c->d_row1 ? c->d_row1 : (c->d_row0 ? c->d_row0 + 1 : nullptr);
     t.nnz1 = c->d_nnz1 ? c->d_nnz1 : (c->d_nnz0 ? c->d_nnz0 + 1 : nullptr);
     t.cta0 = c->d_cta0;
+    t.cta1 = c->d_cta1;
     t.blk0 = c->d_blk0;
     t.blk = c->d_blk;
     t.lcol = c->d_lcol;
@@ -549,7 +552,7 @@ void destroy(jac_ctx* c)
     dfree(c->d_bmap); dfree(c->d_slot_info);
     dfree(c->d_mem_ptr); dfree(c->d_mem_part); dfree(c->d_mem_head); dfree(c->d_loc);
     dfree(c->d_grad); dfree(c->d_orow); dfree(c->d_ocol); dfree(c->d_row0); dfree(c->d_nnz0);
-    dfree(c->d_row1); dfree(c->d_nnz1); dfree(c->d_cta0);
+    dfree(c->d_row1); dfree(c->d_nnz1); dfree(c->d_cta0); dfree(c->d_cta1);
     dfree(c->d_blk0); dfree(c->d_blk); dfree(c->d_lcol); dfree(c->d_trace);
     dfree(c->d_tile_sys); dfree(c->d_sys_pair0); dfree(c->d_cta_pair0); dfree(c->d_cta_sys0); dfree(c->d_bnorm);
     dfree(c->d_cnt); dfree(c->d_mask); dfree(c->d_ksys); dfree(c->d_kpar); dfree(c->d_rel); dfree(c->d_sys_status);
@@ -1077,14 +1080,36 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
         }
         row_cost = &split_cost;
     }
-    if (c->variant == 2)
-        make_tiling(tf, plan, c->rows_per_tile / c->lanes, c->emax, c->grid, tl, row_cost,
-                    sp ? sp->n_own : INT64_MAX, sp ? sp->warp_rows : 1);
+    if (c->variant == 2 && !sp) {
+        make_tiling(tf, plan, c->rows_per_tile / c->lanes, c->emax, c->grid, tl, row_cost);
+    } else if (c->variant == 2) {
+        // Split interface layout: every CTA gets a row range of the interiors and
+        // one of the slot rows (cut on warp boundaries), so each SM runs the same
+        // mix of complete rows and slot rows.  (With the slot rows in the last
+        // CTAs alone, those CTAs' latency-bound tiles left the FP64 pipe to
+        // their SM-mates and no per-CTA cut could balance the sweep.)
+        Tiling t1, t2;
+        const int32_t rpt = c->rows_per_tile / c->lanes;
+        make_tiling(tf, plan, rpt, c->emax, c->grid, t1, row_cost, INT64_MAX, 1, 0, sp->n_own);
+        make_tiling(tf, plan, rpt, c->emax, c->grid, t2, row_cost, sp->n_own, sp->warp_rows, sp->n_own, rows);
+        const int32_t T1 = (int32_t)t1.ntiles();
+        tl = t1;
+        tl.row0.insert(tl.row0.end(), t2.row0.begin() + 1, t2.row0.end());
+        tl.nnz0.insert(tl.nnz0.end(), t2.nnz0.begin() + 1, t2.nnz0.end());
+        tl.tile_part.insert(tl.tile_part.end(), t2.tile_part.begin(), t2.tile_part.end());
+        tl.cta1 = t2.cta0;
+        for (int32_t& v : tl.cta1) v += T1;
+    }
     if (c->variant >= 2) {
         c->ntiles = (int)tl.ntiles();
         // what the balance calibration needs: each CTA's rows and the cost model used
         c->h_cta_row0.resize(c->grid + 1);
         for (int g = 0; g <= c->grid; ++g) c->h_cta_row0[g] = tl.row0[tl.cta0[g]];
+        c->h_cta_row1.clear();
+        if (!tl.cta1.empty()) {
+            c->h_cta_row1.resize(c->grid + 1);
+            for (int g = 0; g <= c->grid; ++g) c->h_cta_row1[g] = tl.row0[tl.cta1[g]];
+        }
         c->h_row_cost.resize(rows);
         for (int64_t r = 0; r < rows; ++r)
             c->h_row_cost[r] = row_cost ? (*row_cost)[r] : default_row_cost(tf.rowptr[r + 1] - tf.rowptr[r]);
@@ -1195,6 +1220,10 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
         CK(nullptr, cudaMemcpy(c->d_row0, tl.row0.data(), tl.row0.size() * 4, cudaMemcpyHostToDevice));
         CK(nullptr, cudaMemcpy(c->d_nnz0, tl.nnz0.data(), tl.nnz0.size() * 4, cudaMemcpyHostToDevice));
         CK(nullptr, cudaMemcpy(c->d_cta0, tl.cta0.data(), tl.cta0.size() * 4, cudaMemcpyHostToDevice));
+        if (!tl.cta1.empty()) {
+            CK(nullptr, dalloc(&c->d_cta1, tl.cta1.size()));
+            CK(nullptr, cudaMemcpy(c->d_cta1, tl.cta1.data(), tl.cta1.size() * 4, cudaMemcpyHostToDevice));
+        }
     }
     CK(nullptr, cudaMemcpy(c->d_rowptr, tf.rowptr.data(), (rows + 1) * 4, cudaMemcpyHostToDevice));
     if (nnz_off) {
@@ -1364,13 +1393,21 @@ static jac_status tune(const jac_opts& o, const std::vector<Geometry>& cand, con
         int64_t nct = 0;
         if (jac_get_trace(best, comp.data(), nullptr, G, &nct) != JAC_OK || nct != G) break;
         std::vector<double> w = best->h_row_cost;
+        // a CTA's rows: one range, or two with a split interface layout
+        auto ranges = [&](int g) {
+            std::pair<int64_t, int64_t> a{best->h_cta_row0[g], best->h_cta_row0[g + 1]}, b{0, 0};
+            if (!best->h_cta_row1.empty()) b = {best->h_cta_row1[g], best->h_cta_row1[g + 1]};
+            return std::make_pair(a, b);
+        };
         for (int g = 0; g < G; ++g) {
-            const int64_t r0 = best->h_cta_row0[g], r1 = best->h_cta_row0[g + 1];
+            const auto rg = ranges(g);
             double W = 0.0;
-            for (int64_t r = r0; r < r1; ++r) W += w[r];
+            for (int64_t r = rg.first.first; r < rg.first.second; ++r) W += w[r];
+            for (int64_t r = rg.second.first; r < rg.second.second; ++r) W += w[r];
             if (W <= 0.0 || !(comp[g] > 0.0)) continue;
             const double f = comp[g] / W;
-            for (int64_t r = r0; r < r1; ++r) w[r] *= f;
+            for (int64_t r = rg.first.first; r < rg.first.second; ++r) w[r] *= f;
+            for (int64_t r = rg.second.first; r < rg.second.second; ++r) w[r] *= f;
         }
         jac_ctx* c = nullptr;
         if (make(best_o, &w, &c) != JAC_OK) break;

@@ -114,6 +114,7 @@ struct DevTiles {
     const int* row1;          // ntiles: ... or, where the tiles skip rows, end row of each tile
     const int* nnz1;          // ntiles: ... and end entry (batched kernel; row0 + 1 / nnz0 + 1 otherwise)
     const int* cta0;          // ctas+1
+    const int* cta1;          // ctas+1: a second tile range per CTA (split layouts: slot tiles), or NULL
     const int* blk0;          // ntiles+1 (halo kernel): int4 offset of each tile's run block
     const int* blk;           // run blocks {xlen, own, nruns, flags} + {src, len, dst, 0} x nruns
     const int* lcol;          // nnz_off tile-local columns (halo kernel)

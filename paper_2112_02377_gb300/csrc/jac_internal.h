@@ -51,6 +51,8 @@ struct Tiling {
     std::vector<int32_t> row0;          // ntiles+1 tile row boundaries
     std::vector<int32_t> nnz0;          // ntiles+1: off-diagonal rowptr at the boundaries
     std::vector<int32_t> cta0;          // ctas+1 tile ranges per CTA
+    std::vector<int32_t> cta1;          // ctas+1: a second tile range per CTA (a split interface block's
+                                        // slot tiles), empty otherwise
     std::vector<int32_t> tile_part;     // partition of each tile
     int64_t ntiles() const { return (int64_t)row0.size() - 1; }
 };
@@ -109,9 +111,10 @@ double default_row_cost(int64_t off_entries);
 // Cost estimate of a slot row (split interface block), same units.
 double slot_row_cost(int64_t entries);
 // Rows at and after align_from are cut only at align_from + multiples of align.
+// Only rows [r_begin, r_end) are tiled (r_end < 0: to the last row).
 void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
                  int64_t ctas, Tiling& t, const std::vector<double>* row_cost = nullptr,
-                 int64_t align_from = INT64_MAX, int32_t align = 1);
+                 int64_t align_from = INT64_MAX, int32_t align = 1, int64_t r_begin = 0, int64_t r_end = -1);
 // Validates the local matrices and builds the split layout for lanes = 32 / warp_rows.
 Error make_split_form(int64_t n, int32_t nsub, const jac_local* sub, int32_t warp_rows, SplitForm& out);
 // Largest number of subdomains holding one row (0 if the input is malformed).

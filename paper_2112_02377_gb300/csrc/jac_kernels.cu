@@ -500,7 +500,16 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
     __syncthreads();
     if (!s_start) return;
 
-    const int tb = t.cta0[blockIdx.x], te = t.cta0[blockIdx.x + 1], nt = te - tb;
+    const int tb = t.cta0[blockIdx.x], nt1 = t.cta0[blockIdx.x + 1] - tb;
+    // a split interface layout gives every CTA a second range: its share of the slot tiles
+    int tb2 = 0, nt2 = 0;
+    if constexpr (SPLIT) {
+        if (t.cta1) {
+            tb2 = t.cta1[blockIdx.x];
+            nt2 = t.cta1[blockIdx.x + 1] - tb2;
+        }
+    }
+    const int nt = nt1 + nt2;
     int ksw = max_sweeps;
     if (!MIXED && !s_test) {
         const long long rem = s_klim - s_k;
@@ -539,7 +548,8 @@ k_persistent(DevMat m, DevVec v, DevTiles t, JacCtl* ctl, int max_sweeps)
                 }
                 // ---- issue job j
                 const int sw = (int)(j / nt);
-                const int ti = tb + (int)(j - (long long)sw * nt);
+                const int tj = (int)(j - (long long)sw * nt);
+                const int ti = tj < nt1 ? tb + tj : tb2 + (tj - nt1);
                 const int ph = phase_of(MIXED, MIXED ? (phase0 + sw) % inner : 0, inner);
                 const bool fp64 = PART == 1 ? true : PART == 2 ? false : (ph == PH_P64 || ph == PH_P64R);
                 unsigned char* st = smem + sidx * L.bytes;

@@ -344,7 +344,8 @@ double slot_row_cost(int64_t entries)
 }
 
 void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, int32_t max_entries,
-                 int64_t ctas, Tiling& t, const std::vector<double>* row_cost, int64_t align_from, int32_t align)
+                 int64_t ctas, Tiling& t, const std::vector<double>* row_cost, int64_t align_from, int32_t align,
+                 int64_t r_begin, int64_t r_end)
 {
     auto aligned_up = [&](int64_t r) -> int64_t {
         if (align <= 1 || r <= align_from) return r;
@@ -353,28 +354,30 @@ void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, 
     t = Tiling();
     t.rows_per_tile = rows_per_tile;
     t.max_entries = max_entries;
-    const int64_t n = tf.n;
+    const int64_t n = r_end < 0 ? tf.n : r_end;
+    const int64_t b0 = r_begin;
     // CTA row ranges: contiguous, cut at row granularity so that every CTA
-    // carries the same estimated cost.
-    std::vector<double> pre(n + 1, 0.0);
-    for (int64_t r = 0; r < n; ++r) {
+    // carries the same estimated cost (pre[r - b0]: cost of rows b0 .. r-1).
+    std::vector<double> pre(n - b0 + 1, 0.0);
+    for (int64_t r = b0; r < n; ++r) {
         const double w = row_cost ? (*row_cost)[r] : default_row_cost(tf.rowptr[r + 1] - tf.rowptr[r]);
-        pre[r + 1] = pre[r] + w;
+        pre[r - b0 + 1] = pre[r - b0] + w;
     }
-    std::vector<int64_t> rb(ctas + 1, 0);
+    std::vector<int64_t> rb(ctas + 1, b0);
     rb[ctas] = n;
     {
-        int64_t cur = 0;
+        int64_t cur = b0;
+        const double tot = pre[n - b0];
         for (int64_t g = 1; g < ctas; ++g) {
-            const double target = pre[n] * (double)g / (double)ctas;
-            while (cur < n && pre[cur] + 0.5 * (pre[cur + 1] - pre[cur]) < target) ++cur;
+            const double target = tot * (double)g / (double)ctas;
+            while (cur < n && pre[cur - b0] + 0.5 * (pre[cur - b0 + 1] - pre[cur - b0]) < target) ++cur;
             cur = aligned_up(cur);
             rb[g] = cur;
         }
     }
     // Tiles: at most rows_per_tile rows and max_entries staged entries, never
     // crossing a partition or a CTA boundary.
-    t.row0.push_back(0);
+    t.row0.push_back((int32_t)b0);
     t.cta0.assign(ctas + 1, 0);
     int64_t p = 0;
     const int64_t P = plan.nparts();
