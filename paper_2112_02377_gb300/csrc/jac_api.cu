@@ -1083,22 +1083,7 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
     if (c->variant == 2 && !sp) {
         make_tiling(tf, plan, c->rows_per_tile / c->lanes, c->emax, c->grid, tl, row_cost);
     } else if (c->variant == 2) {
-        // Split interface layout: every CTA gets a row range of the interiors and
-        // one of the slot rows (cut on warp boundaries), so each SM runs the same
-        // mix of complete rows and slot rows.  (With the slot rows in the last
-        // CTAs alone, those CTAs' latency-bound tiles left the FP64 pipe to
-        // their SM-mates and no per-CTA cut could balance the sweep.)
-        Tiling t1, t2;
-        const int32_t rpt = c->rows_per_tile / c->lanes;
-        make_tiling(tf, plan, rpt, c->emax, c->grid, t1, row_cost, INT64_MAX, 1, 0, sp->n_own);
-        make_tiling(tf, plan, rpt, c->emax, c->grid, t2, row_cost, sp->n_own, sp->warp_rows, sp->n_own, rows);
-        const int32_t T1 = (int32_t)t1.ntiles();
-        tl = t1;
-        tl.row0.insert(tl.row0.end(), t2.row0.begin() + 1, t2.row0.end());
-        tl.nnz0.insert(tl.nnz0.end(), t2.nnz0.begin() + 1, t2.nnz0.end());
-        tl.tile_part.insert(tl.tile_part.end(), t2.tile_part.begin(), t2.tile_part.end());
-        tl.cta1 = t2.cta0;
-        for (int32_t& v : tl.cta1) v += T1;
+        make_split_tiling(*sp, c->rows_per_tile / c->lanes, c->emax, c->grid, tl, row_cost);
     }
     if (c->variant >= 2) {
         c->ntiles = (int)tl.ntiles();

@@ -117,6 +117,10 @@ void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, 
                  int64_t align_from = INT64_MAX, int32_t align = 1, int64_t r_begin = 0, int64_t r_end = -1);
 // Validates the local matrices and builds the split layout for lanes = 32 / warp_rows.
 Error make_split_form(int64_t n, int32_t nsub, const jac_local* sub, int32_t warp_rows, SplitForm& out);
+// Tiles of a split layout: the interiors' tiles, then the slot rows' tiles
+// (on warp boundaries); each CTA owns a range of each (cta0, cta1).
+void make_split_tiling(const SplitForm& f, int32_t rows_per_tile, int32_t max_entries, int64_t ctas, Tiling& t,
+                       const std::vector<double>* row_cost = nullptr);
 // Largest number of subdomains holding one row (0 if the input is malformed).
 int32_t split_max_multiplicity(int64_t n, int32_t nsub, const jac_local* sub);
 HostCSR transpose_csr(const HostCSR& A);

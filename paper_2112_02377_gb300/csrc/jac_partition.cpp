@@ -413,6 +413,26 @@ void make_tiling(const ScaledForm& tf, const Plan& plan, int32_t rows_per_tile, 
     for (int64_t i = 0; i <= nt; ++i) t.nnz0[i] = tf.rowptr[t.row0[i]];
 }
 
+void make_split_tiling(const SplitForm& f, int32_t rows_per_tile, int32_t max_entries, int64_t ctas, Tiling& t,
+                       const std::vector<double>* row_cost)
+{
+    // Every CTA gets a row range of the interiors (cta0) and one of the slot
+    // rows (cta1, cut on warp boundaries), so each SM runs the same mix of
+    // complete rows and slot rows.  With the slot rows in the last CTAs alone,
+    // those CTAs' latency-bound tiles left the SM's FP64 pipe to their
+    // SM-mates, and no per-CTA cut could balance the sweep.
+    Tiling t2;
+    make_tiling(f.tf, f.plan, rows_per_tile, max_entries, ctas, t, row_cost, INT64_MAX, 1, 0, f.n_own);
+    make_tiling(f.tf, f.plan, rows_per_tile, max_entries, ctas, t2, row_cost, f.n_own, f.warp_rows, f.n_own,
+                f.tf.n);
+    const int32_t T1 = (int32_t)t.ntiles();
+    t.row0.insert(t.row0.end(), t2.row0.begin() + 1, t2.row0.end());
+    t.nnz0.insert(t.nnz0.end(), t2.nnz0.begin() + 1, t2.nnz0.end());
+    t.tile_part.insert(t.tile_part.end(), t2.tile_part.begin(), t2.tile_part.end());
+    t.cta1 = t2.cta0;
+    for (int32_t& v : t.cta1) v += T1;
+}
+
 void make_windows(const ScaledForm& tf, const Tiling& t, int32_t xcap, int32_t maxruns, int32_t emax, Windows& w)
 {
     const int64_t nt = t.ntiles();

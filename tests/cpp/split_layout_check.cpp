@@ -147,6 +147,26 @@ static int check_case(int64_t n, int nsub, int max_extra, int warp_rows)
         }
         CHECK(t.row0.back() == tf.n, "tiles do not cover the kernel rows");
     }
+    // split tiling: interior tiles then slot tiles, each CTA a range of both
+    for (int64_t ctas : {1, 7, 64, 301}) {
+        Tiling t;
+        make_split_tiling(f, 256, 1536, ctas, t);
+        const int64_t T = t.ntiles();
+        CHECK(t.row0.front() == 0 && t.row0.back() == tf.n, "split tiles do not cover the kernel rows");
+        CHECK((int64_t)t.cta0.size() == ctas + 1 && (int64_t)t.cta1.size() == ctas + 1, "CTA range arrays");
+        const int64_t T1 = t.cta0[ctas];
+        CHECK(t.cta0[0] == 0 && t.cta1[0] == T1 && t.cta1[ctas] == T, "CTA ranges do not cover the tiles");
+        for (int64_t g = 0; g < ctas; ++g)
+            CHECK(t.cta0[g + 1] >= t.cta0[g] && t.cta1[g + 1] >= t.cta1[g], "CTA ranges not monotone");
+        CHECK(T1 == 0 || t.row0[T1] == f.n_own, "interior tiles end at %lld, not at n_own", (long long)t.row0[T1]);
+        for (int64_t i2 = 0; i2 < T; ++i2) {
+            const int64_t r0 = t.row0[i2], r1 = t.row0[i2 + 1];
+            CHECK(r1 > r0, "empty split tile");
+            CHECK(t.nnz0[i2] == tf.rowptr[r0], "split tile entry offset");
+            if (i2 < T1) CHECK(r1 <= f.n_own, "an interior-range tile holds slot rows");
+            else CHECK(r0 >= f.n_own && (r0 - f.n_own) % warp_rows == 0, "slot tile off a warp boundary");
+        }
+    }
     return 0;
 }
 
