@@ -1272,6 +1272,56 @@ static jac_status setup_core(const Plan& plan, const ScaledForm& tf, int64_t n, 
 
 
 // One context with fixed options from a CSR matrix.
+// The host-side work of jac_setup that no kernel geometry changes: the
+// validated matrix, the splitting and the scaled form.  The autotuner builds
+// it once and sets every candidate up from it.
+struct Prepared {
+    HostView hv;
+    HostCSR M;
+    Plan plan;
+    ScaledForm tf;
+    int64_t halo_entries = 0;
+};
+
+static jac_status prepare(const jac_csr* A, jac_splitting s, int32_t nparts, const jac_opts& o, int dev,
+                          Prepared& p)
+{
+    DeviceGuard guard(dev);
+    jac_status st = host_view(A, p.hv, nullptr);
+    if (st != JAC_OK) return st;
+    Error e = host_csr_from_abi(&p.hv.csr, o.transpose != 0, p.M);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    e = make_plan(p.M, s, nparts, o, p.plan);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    e = make_scaled_form(p.M, p.plan, p.tf);
+    if (!e.ok()) return fail(nullptr, e.st, e.msg);
+    std::vector<int64_t> rp, rc;
+    std::vector<int32_t> rf;
+    dependency_lists(p.M, p.plan, rp, rf, rc);
+    p.halo_entries = (int64_t)rc.size();
+    return JAC_OK;
+}
+
+static jac_status setup_prepared(const Prepared& p, const jac_csr* A, const double* b, jac_opts o, int dev,
+                                 const std::vector<double>* row_cost, jac_ctx** out)
+{
+    *out = nullptr;
+    if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
+    jac_status st = check_opts(o, nullptr);
+    if (st != JAC_OK) return st;
+    DeviceGuard guard(dev);
+    // without transpose, M is the caller's pattern (the adjoint gradient's)
+    return setup_core(p.plan, p.tf, p.M.n, p.M.nnz(), p.halo_entries, nullptr, o.transpose ? nullptr : &p.M, b,
+                      A->memory, o, dev, row_cost, out);
+}
+
+static jac_status device_of(const jac_opts& o, int* dev)
+{
+    *dev = o.device;
+    if (*dev < 0 && cudaGetDevice(dev) != cudaSuccess) return fail(nullptr, JAC_ECUDA, "no CUDA device");
+    return JAC_OK;
+}
+
 static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting s, int32_t nparts, jac_opts o,
                                const std::vector<double>* row_cost, jac_ctx** out)
 {
@@ -1279,29 +1329,13 @@ static jac_status setup_single(const jac_csr* A, const double* b, jac_splitting 
     if (o.timeout_cycles == 0) o.timeout_cycles = 4000000000ull;
     jac_status st = check_opts(o, nullptr);
     if (st != JAC_OK) return st;
-    int dev = o.device;
-    if (dev < 0) {
-        if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, JAC_ECUDA, "no CUDA device");
-    }
-    DeviceGuard guard(dev);
-    HostView hv;
-    st = host_view(A, hv, nullptr);
+    int dev = 0;
+    st = device_of(o, &dev);
     if (st != JAC_OK) return st;
-    HostCSR M;
-    Error e = host_csr_from_abi(&hv.csr, o.transpose != 0, M);
-    if (!e.ok()) return fail(nullptr, e.st, e.msg);
-    Plan plan;
-    e = make_plan(M, s, nparts, o, plan);
-    if (!e.ok()) return fail(nullptr, e.st, e.msg);
-    ScaledForm tf;
-    e = make_scaled_form(M, plan, tf);
-    if (!e.ok()) return fail(nullptr, e.st, e.msg);
-    std::vector<int64_t> rp, rc;
-    std::vector<int32_t> rf;
-    dependency_lists(M, plan, rp, rf, rc);
-    // without transpose, M is the caller's pattern (the adjoint gradient's)
-    return setup_core(plan, tf, M.n, M.nnz(), (int64_t)rc.size(), nullptr, o.transpose ? nullptr : &M, b,
-                      A->memory, o, dev, row_cost, out);
+    Prepared p;
+    st = prepare(A, s, nparts, o, dev, p);
+    if (st != JAC_OK) return st;
+    return setup_prepared(p, A, b, o, dev, row_cost, out);
 }
 
 // Autotuner: set up every candidate geometry with `make`, time a few sweeps
@@ -1427,6 +1461,16 @@ try {
     const bool async = (o.sync == JAC_SYNC_ASYNC);
     // local stopping runs in the grid-synchronised 256-thread geometry with 1, 2 or 4 lanes
     const bool local_stop = (o.stop == JAC_STOP_LOCAL);
+    // the host-side work, once for every candidate (after the options every
+    // candidate shares are checked)
+    jac_status st0 = check_opts(o, nullptr);
+    if (st0 != JAC_OK) return st0;
+    int dev = 0;
+    st0 = device_of(o, &dev);
+    if (st0 != JAC_OK) return st0;
+    Prepared prep;
+    st0 = prepare(A, s, nparts, o, dev, prep);
+    if (st0 != JAC_OK) return st0;
     // the automatic lane count (its own arithmetic: see jac_opts.lanes_per_row)
     int la = o.lanes_per_row;
     if (la == 0) {
@@ -1435,7 +1479,7 @@ try {
         op.autotune = 0;
         op.variant = 2;
         op.tile_rows = 256;
-        if (setup_single(A, b, s, nparts, op, nullptr, &probe) == JAC_OK) {
+        if (setup_prepared(prep, A, b, op, dev, nullptr, &probe) == JAC_OK) {
             la = probe->lanes;
             jac_free(probe);
         }
@@ -1482,7 +1526,7 @@ try {
                 }
     }
     return tune(o, cand, [&](const jac_opts& oc, const std::vector<double>* rc, jac_ctx** pc) {
-        return setup_single(A, b, s, nparts, oc, rc, pc);
+        return setup_prepared(prep, A, b, oc, dev, rc, pc);
     }, out);
 } catch (...) {
     return host_exception(nullptr);
